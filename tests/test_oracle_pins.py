@@ -1,0 +1,383 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself.  Each pins one step against an
+independent definition: quadrature, closed forms, LAPACK pivoted Cholesky, an
+explicit least-squares solve, a plane-wave Coulomb identity, grid-exact
+(FFTDF) ERIs on the supercell, the Gamma-point supercell, symmetry and momentum
+selection rules.  The mutation tests at the end plant plausible mistakes in the
+oracle and check that a pin catches each of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.linalg.lapack as lapack
+
+import oracle as O
+from paper_2601_16379_gb300 import workloads as W
+
+
+# ----------------------------------------------------------------- fixtures
+def tiny_cell(kmesh=2, mesh=10, shells=None):
+    if shells is None:
+        shells = [W.Shell(0, 0, (0.6,), (1.0,)), W.Shell(1, 0, (0.9,), (1.0,))]
+    return W.custom_cell(5.0, [[0, 0, 0], [0.37, 0.52, 0.21]], shells, kmesh, mesh)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    cell = tiny_cell()
+    phi = O.bloch_ao(cell)
+    ips, nfound = O.select_ips(phi, 400, seed=7, chol_tol=1e-13)
+    return cell, phi, ips, nfound
+
+
+@pytest.fixture(scope="module")
+def tiny5():
+    """5 AOs (s, s, p) on a 3x3x3 mesh (so that -q differs from q): 12 points
+    give full-rank Pi^q at every q."""
+    cell = tiny_cell(kmesh=3, shells=[W.Shell(0, 0, (0.6,), (1.0,)), W.Shell(1, 0, (0.9,), (1.0,)),
+                             W.Shell(0, 1, (1.2,), (1.0,))])
+    phi = O.bloch_ao(cell)
+    ips, nfound = O.select_ips(phi, 12, seed=7, chol_tol=1e-13)
+    return cell, phi, ips, nfound
+
+
+@pytest.fixture(scope="module")
+def c1run():
+    wl = W.workload("c1")
+    r = O.run_isdf(wl.cell, wl.n_p, wl.seed)
+    return wl, r
+
+
+# ------------------------------------------------------- O-1 basis functions
+def test_gaussian_closed_forms():
+    """Normalised Cartesian GTOs at a point against textbook closed forms."""
+    a = 0.8
+    shells = [W.Shell(0, 0, (a,), (1.0,)), W.Shell(0, 1, (a,), (1.0,)), W.Shell(0, 2, (a,), (1.0,))]
+    cell = W.custom_cell(10.0, [[0.1, 0.2, 0.3]], shells, 1, 4)
+    A = cell.coords[0]
+    pt = np.array([[1.3, 2.9, 2.2]])
+    x, y, z = (pt[0] - A)
+    g = math.exp(-a * (x * x + y * y + z * z)) * (2 * a / math.pi) ** 0.75
+    ref = [g, 2 * math.sqrt(a) * x * g, 2 * math.sqrt(a) * y * g, 2 * math.sqrt(a) * z * g,
+           4 * a / math.sqrt(3) * x * x * g, 4 * a * x * y * g, 4 * a * x * z * g,
+           4 * a / math.sqrt(3) * y * y * g, 4 * a * y * z * g, 4 * a / math.sqrt(3) * z * z * g]
+    v = O.ao_values(cell, pt)[:, 0]
+    assert np.allclose(v, ref, rtol=1e-14, atol=0)
+
+
+def test_normalisation_by_quadrature():
+    """Grid quadrature of |phi|^2 over a large cell at Gamma is 1 for s, p and d."""
+    shells = [W.Shell(0, 0, (1.5,), (1.0,)), W.Shell(0, 1, (1.5,), (1.0,)), W.Shell(0, 2, (1.5,), (1.0,))]
+    cell = W.custom_cell(11.0, [[0.5, 0.5, 0.5]], shells, 1, 48)
+    phi = O.bloch_ao(cell)[0]
+    norms = np.sum(np.abs(phi) ** 2, axis=1) * cell.volume / cell.ngrid
+    assert np.allclose(norms, 1.0, atol=1e-10)
+
+
+def test_bloch_phase_and_time_reversal():
+    """Phi^k(r + a_i) = e^{i k.a_i} Phi^k(r) and Phi^{-k} = conj(Phi^k) (Eq. 1)."""
+    cell = tiny_cell(kmesh=3, mesh=6, shells=[W.Shell(0, 0, (0.7,), (1.0,)), W.Shell(1, 1, (1.1,), (1.0,))])
+    pts = O.grid_points(cell)[::17]
+    phi = O.bloch_ao(cell, pts=pts)
+    m = O.kmesh_indices(cell.kmesh)
+    for i in range(3):
+        shifted = O.bloch_ao(cell, pts=pts + cell.lattice[i][None, :])
+        phase = np.exp(2j * np.pi * m[:, i] / cell.kmesh[i])
+        assert np.allclose(shifted, phase[:, None, None] * phi, atol=1e-12, rtol=0)
+    km = O.k_minus_table(cell.kmesh)
+    for k in range(cell.nkpts):
+        assert np.allclose(phi[km[0, k]], phi[k].conj(), atol=1e-13, rtol=0)
+
+
+def test_k_sum_is_supercell_periodisation():
+    """sum_k Phi^k(r) = Nk sum_S phi~(r - n_k S a): the phases select the supercell lattice."""
+    cell = tiny_cell(kmesh=2, mesh=6)
+    pts = O.grid_points(cell)[::7]
+    phi = O.bloch_ao(cell, pts=pts)
+    L = O.lattice_range(cell)
+    direct = np.zeros((cell.nao, pts.shape[0]))
+    rng = range(-2 * L[0], 2 * L[0] + 1)
+    for s0 in rng:
+        for s1 in rng:
+            for s2 in rng:
+                n = np.array([s0, s1, s2])
+                if np.any(np.abs(n) > L):
+                    continue
+                if np.any(n % 2 != 0):
+                    continue
+                direct += O.ao_values(cell, pts - (n @ cell.lattice)[None, :])
+    assert np.allclose(phi.sum(axis=0), cell.nkpts * direct, atol=1e-12, rtol=0)
+
+
+# --------------------------------------------------------- O-3 point choice
+def test_splitmix64_published_values():
+    """SplitMix64 (Steele, Lea & Flood 2014) from seed 1234567: the first outputs."""
+    gamma = 0x9E3779B97F4A7C15
+    s = 1234567
+    outs = [int(O.splitmix64(np.uint64((s + i * gamma) % 2**64))) for i in range(3)]
+    assert outs == [6457827717110365317, 3203168211198807973, 9817491932198370423]
+
+
+def test_ip_selection_matches_lapack_pstrf():
+    """Greedy pivots equal LAPACK dpstrf on the explicit Gram K = |D|^2 (no ties)."""
+    cell = W.custom_cell(4.3, [[0.0, 0.0, 0.0], [0.31, 0.57, 0.12]],
+                         [W.Shell(0, 0, (0.9,), (1.0,)), W.Shell(1, 0, (1.4,), (1.0,)), W.Shell(0, 1, (1.2,), (1.0,))],
+                         (2, 1, 1), 6)
+    phi = O.bloch_ao(cell)
+    F = phi.reshape(-1, cell.ngrid)
+    K = np.abs(F.conj().T @ F) ** 2
+    n_p = 24
+    ips, nf = O.select_ips(phi, n_p, seed=3, chol_tol=1e-14)
+    assert nf == n_p
+    _, piv, rank, info = lapack.dpstrf(K.copy(), lower=1, tol=-1.0)
+    assert np.array_equal(ips, piv[:n_p] - 1)
+
+
+def test_ip_residual_trace_decreases(tiny):
+    cell, phi, ips, nf = tiny
+    F = phi.reshape(-1, cell.ngrid)
+    K = np.abs(F.conj().T @ F) ** 2
+    traces = []
+    for j in range(1, 40, 6):
+        S = ips[:j]
+        Kss = K[np.ix_(S, S)]
+        resid = np.trace(K) - np.trace(K[:, S] @ np.linalg.solve(Kss, K[S, :]))
+        traces.append(resid)
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(traces, traces[1:]))
+
+
+def test_pchol_matches_lapack_zpstrf():
+    rng = np.random.default_rng(5)
+    Z = rng.standard_normal((30, 17)) + 1j * rng.standard_normal((30, 17))
+    A = Z @ Z.conj().T
+    L, perm, r = O.pchol(A, 1e-12)
+    assert r == 17
+    assert np.allclose(L @ L.conj().T, A, atol=1e-10 * np.abs(A).max())
+    _, piv, rank, info = lapack.zpstrf(A.copy(), lower=1, tol=1e-12 * np.abs(np.diag(A)).max() / 30)
+    assert rank == 17
+    assert np.array_equal(perm, piv[:17] - 1)
+
+
+# ------------------------------------------------------------------ O-4 fit
+def _explicit_ls(cell, phi, ips, q):
+    """Pair x IP matrix A^q and pair densities rho^q(r) written out, then lstsq."""
+    X = O.interp_vectors(phi, ips)
+    km = O.k_minus_table(cell.kmesh)
+    rows_A, rows_rho = [], []
+    for k in range(cell.nkpts):
+        kq = km[k, q]
+        for mu in range(cell.nao):
+            for nu in range(cell.nao):
+                rows_A.append(X[k][:, mu] * X[kq][:, nu].conj())
+                rows_rho.append(phi[k][mu] * phi[kq][nu].conj())
+    A = np.array(rows_A)
+    rho = np.array(rows_rho)
+    zeta, *_ = np.linalg.lstsq(A, rho, rcond=None)
+    return A, rho, zeta
+
+
+def test_fit_equals_explicit_least_squares(tiny5):
+    """Pi^q, eta^q (Eqs. 4-5 by direct k-sums) and the solve equal an explicit lstsq (Eq. 2-3)."""
+    cell, phi, ips, nf = tiny5
+    sel = ips[:12]
+    X = O.interp_vectors(phi, sel)
+    Pi = O.metric_pi(X, cell.kmesh)
+    eta = O.rhs_eta(X, phi, cell.kmesh)
+    zeta, ranks = O.fit_zeta(Pi, eta, 1e-14)
+    for q in (0, 3, 5):
+        A, rho, zls = _explicit_ls(cell, phi, sel, q)
+        assert np.allclose(Pi[q], A.conj().T @ A, atol=1e-12 * np.abs(Pi[q]).max())
+        assert np.allclose(eta[q], A.conj().T @ rho, atol=1e-12 * np.abs(eta[q]).max())
+        assert ranks[q] == 12
+        assert np.allclose(zeta[q], zls, atol=1e-7 * np.abs(zls).max())
+
+
+def test_pi_zeta_conjugate_symmetry(c1run):
+    wl, r = c1run
+    km = O.k_minus_table(wl.cell.kmesh)
+    for q in range(wl.cell.nkpts):
+        assert np.allclose(r["Pi"][km[0, q]], r["Pi"][q].conj(), atol=1e-13 * np.abs(r["Pi"]).max())
+        h = r["Pi"][q]
+        assert np.allclose(h, h.conj().T, atol=1e-13 * np.abs(h).max())
+        assert np.linalg.eigvalsh(h).min() > -1e-12 * np.abs(h).max()
+
+
+# -------------------------------------------------------------- O-5 Coulomb
+def test_coulomb_plane_waves():
+    """zeta_I = e^{i(q+G_I).r} gives V_IJ = Omega 4 pi/|q+G_I|^2 delta_IJ exactly (Eq. 6)."""
+    cell = W.custom_cell(4.0, [[0, 0, 0]], [W.Shell(0, 0, (1.0,), (1.0,))], (3, 1, 2), (6, 8, 4))
+    pts = O.grid_points(cell)
+    for q in (0, 1, 4):
+        mq = O.kmesh_indices(cell.kmesh)[q]
+        Gs = [np.array(g) for g in ([1, 0, 0], [0, -2, 1], [2, 3, -1], [-3, 0, 0])]
+        b = O.reciprocal(cell.lattice)
+        rows = []
+        vals = []
+        for G in Gs:
+            kvec = (mq / np.asarray(cell.kmesh) + G) @ b
+            rows.append(np.exp(1j * pts @ kvec))
+            vals.append(cell.volume * 4 * np.pi / (kvec @ kvec))
+        V = O.coulomb_metric(cell, np.array(rows)[None], [q])[0]
+        assert np.allclose(V, np.diag(vals), rtol=1e-12, atol=1e-12 * max(vals))
+
+
+def test_coulomb_hermitian_psd(c1run):
+    wl, r = c1run
+    km = O.k_minus_table(wl.cell.kmesh)
+    for q in range(wl.cell.nkpts):
+        V = r["V"][q]
+        s = np.abs(V).max()
+        assert np.allclose(V, V.conj().T, atol=1e-12 * s)
+        assert np.linalg.eigvalsh(V).min() > -1e-11 * s
+        assert np.allclose(r["V"][km[0, q]], V.conj(), atol=1e-11 * s)
+
+
+# ---------------------------------------------------------- end-to-end pins
+def test_isdf_exact_limit_and_convergence(tiny):
+    """With N_P at the pair-space rank the ISDF ERIs equal the grid-exact
+    supercell ERIs; below it the error falls as N_P grows (Section III.A)."""
+    cell, phi, ips, nf = tiny
+    frag = W.make_fragment(cell, 11, 0, 3)
+    ref = O.fftdf_fragment_eri(cell, frag.C)
+    errs = []
+    for n_p in (8, 24, 64, nf):
+        r = O.run_isdf(cell, n_p, 7, solve_tol=1e-14, ips=ips[:n_p], phi=phi)
+        eri = O.fragment_eri(r["X"], r["V"], frag.C, cell.kmesh)
+        errs.append(np.abs(eri - ref).max())
+    assert errs[-1] < 1e-9 * np.abs(ref).max()
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+
+
+def test_gamma_supercell_equivalence(tiny5):
+    """k-ISDF on the Nk mesh equals Gamma-point ISDF of the Nk-image supercell
+    with the translated points (Algorithms 1 and 2, supercell picture).  Exact
+    when every Pi^q has full rank, so that no truncation mixes the q blocks."""
+    cell, phi, ips, nf = tiny5
+    n_p = 12
+    frag = W.make_fragment(cell, 11, 1, 3)
+    r = O.run_isdf(cell, n_p, 7, solve_tol=1e-14, ips=ips[:n_p], phi=phi)
+    eri_k = O.fragment_eri(r["X"], r["V"], frag.C, cell.kmesh)
+    sc = O.supercell(cell)
+    rs = O.run_isdf(sc, cell.nkpts * n_p, 0, solve_tol=1e-14, ips=O.supercell_ips(cell, ips[:n_p]))
+    eri_g = O.fragment_eri(rs["X"], rs["V"], O.supercell_coefficients(cell, frag.C), sc.kmesh)
+    assert np.abs(eri_k - eri_g).max() < 1e-10 * np.abs(eri_k).max()
+
+
+def test_eri_symmetries(c1run):
+    wl, r = c1run
+    f = W.make_fragment(wl.cell, wl.seed, 3, 5)
+    eri = O.fragment_eri(r["X"], r["V"], f.C, wl.cell.kmesh)
+    s = np.abs(eri).max()
+    assert np.allclose(eri, eri.transpose(2, 3, 0, 1), atol=1e-9 * s)            # (pq|rs) = (rs|pq)
+    assert np.allclose(eri, eri.transpose(1, 0, 3, 2).conj(), atol=1e-9 * s)     # = conj((qp|sr))
+    H = eri.transpose(1, 0, 2, 3).reshape(25, 25)                                 # H_(qp),(rs)
+    assert np.allclose(H, H.conj().T, atol=1e-9 * s)
+    assert np.linalg.eigvalsh(H).min() > -1e-9 * s
+
+
+def test_real_orbitals_give_real_eightfold(c1run):
+    wl, r = c1run
+    f = W.make_real_fragment(wl.cell, 17, 4)
+    eri = O.fragment_eri(r["X"], r["V"], f.C, wl.cell.kmesh)
+    s = np.abs(eri).max()
+    assert np.abs(eri.imag).max() < 1e-9 * s
+    e = eri.real
+    for perm in [(1, 0, 2, 3), (0, 1, 3, 2), (2, 3, 0, 1), (3, 2, 1, 0)]:
+        assert np.allclose(e, e.transpose(perm), atol=1e-9 * s)
+
+
+def test_momentum_conservation(c1run):
+    wl, r = c1run
+    f, kp = W.make_singlek_fragment(wl.cell, 23, 6)
+    eri = O.fragment_eri(r["X"], r["V"], f.C, wl.cell.kmesh)
+    m = O.kmesh_indices(wl.cell.kmesh)
+    km = np.asarray(wl.cell.kmesh)
+    s = np.abs(eri).max()
+    assert s > 0
+    for p in range(6):
+        for q in range(6):
+            for rr in range(6):
+                for t in range(6):
+                    tot = (m[kp[p]] - m[kp[q]] + m[kp[rr]] - m[kp[t]]) % km
+                    if np.any(tot != 0):
+                        assert abs(eri[p, q, rr, t]) < 1e-12 * s
+
+
+def test_traces_signs_and_cheap_J(c1run):
+    wl, r = c1run
+    f = wl.fragments[0]
+    eri = O.fragment_eri(r["X"], r["V"], f.C, wl.cell.kmesh)
+    ej, ek = O.traces(eri, f.gamma)
+    assert ej > 0 and ek < 0
+    M = O.pair_tensor(O.fragment_T(r["X"], f.C), wl.cell.kmesh)
+    # |V| ~ 1e8 |E| at this truncation, so rounding in the two orders differs at ~1e-16 * 1e8
+    assert abs(O.cheap_J(M, r["V"], f.gamma, wl.cell.nkpts) - ej) < 1e-9 * abs(ej)
+
+
+def test_nk1_is_gamma_point_isdf():
+    """At Nk = 1 the fit is textbook Gamma-point ISDF of real pair products."""
+    cell = tiny_cell(kmesh=1, mesh=10)
+    phi = O.bloch_ao(cell)
+    assert np.abs(phi.imag).max() == 0.0
+    ips, _ = O.select_ips(phi, 3, 1)
+    A, rho, zls = _explicit_ls(cell, phi, ips, 0)
+    r = O.run_isdf(cell, 3, 1, solve_tol=1e-14, ips=ips, phi=phi)
+    assert np.allclose(r["zeta"][0], zls, atol=1e-8 * np.abs(zls).max())
+
+
+# ------------------------------------------------------------ mutation tests
+def _mutant_eta(X, phi, kmesh, qs=None, g=None):
+    """eta with k+q in place of k-q (a plausible index mistake)."""
+    g = O.g_values(X, phi)
+    kp = O.k_plus_table(kmesh)
+    qs = range(X.shape[0]) if qs is None else qs
+    return np.array([sum(g[k] * g[kp[k, q]].conj() for k in range(X.shape[0])) for q in qs])
+
+
+def _mutant_pair(T, kmesh, qs=None):
+    """M without the conjugate on the second factor."""
+    kp = O.k_plus_table(kmesh)
+    nk, npt, nf = T.shape
+    qs = range(nk) if qs is None else qs
+    out = []
+    for Q in qs:
+        acc = np.zeros((nf, nf, npt), np.complex128)
+        for k in range(nk):
+            acc += np.einsum("ip,iq->pqi", T[kp[k, Q]], T[k])
+        out.append(acc.reshape(nf * nf, npt))
+    return np.array(out)
+
+
+def test_mutation_eta_index_caught(tiny5):
+    cell, phi, ips, nf = tiny5
+    sel = ips[:12]
+    A, rho, zls = _explicit_ls(cell, phi, sel, 3)
+    X = O.interp_vectors(phi, sel)
+    bad = _mutant_eta(X, phi, cell.kmesh)[3]
+    assert not np.allclose(bad, A.conj().T @ rho, atol=1e-6 * np.abs(bad).max())
+
+
+def test_mutation_pair_conjugate_caught(tiny, monkeypatch):
+    cell, phi, ips, nf = tiny
+    frag = W.make_fragment(cell, 11, 0, 3)
+    ref = O.fftdf_fragment_eri(cell, frag.C)
+    r = O.run_isdf(cell, nf, 7, solve_tol=1e-14, ips=ips, phi=phi)
+    monkeypatch.setattr(O.isdf_oracle, "pair_tensor", _mutant_pair)
+    eri = O.isdf_oracle.fragment_eri(r["X"], r["V"], frag.C, cell.kmesh)
+    assert np.abs(eri - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_mutation_fft_sign_caught(monkeypatch):
+    cell = W.custom_cell(4.0, [[0, 0, 0]], [W.Shell(0, 0, (1.0,), (1.0,))], (2, 1, 1), (6, 6, 6))
+    pts = O.grid_points(cell)
+    b = O.reciprocal(cell.lattice)
+    kvec = (np.array([1, 0, 0]) / np.array([2, 1, 1]) + np.array([1, 0, 0])) @ b
+    z = np.exp(1j * pts @ kvec)[None, None]
+    good = O.coulomb_metric(cell, z, [1])[0, 0, 0]
+    monkeypatch.setattr(np.fft, "fftn", lambda a, axes=None: np.fft.ifftn(a, axes=axes) * np.prod([a.shape[i] for i in axes]))
+    bad = O.coulomb_metric(cell, z, [1])[0, 0, 0]
+    assert abs(good - cell.volume * 4 * np.pi / (kvec @ kvec)) < 1e-9 * abs(good)
+    assert abs(bad - good) > 1e-3 * abs(good)
