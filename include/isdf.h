@@ -1,0 +1,163 @@
+/*
+ * isdf.h -- C ABI of the GB300 k-ISDF fragment-ERI library (libisdf.so).
+ *
+ * The library computes, on one GPU, the electron-repulsion integrals of
+ * embedding / local-correlation fragments through translation-symmetry-adapted
+ * interpolative separable density fitting (k-point FFTISDF).  The four steps
+ * follow Section II of the paper:
+ *
+ *   isdf_build_points    Bloch GTOs on the grid (Eq. 1), interpolation points by
+ *                        pivoted Cholesky of the pair products (Section II.A),
+ *                        interpolating vectors X^k_{I mu} = phi^k_mu(r_I).
+ *   isdf_fit_zeta        least-squares fit Pi^q xi^q = eta^q (Eqs. 2-5) with the
+ *                        k-sums done as convolutions over the k-mesh (Algorithm 1).
+ *   isdf_coulomb_metric  Coulomb kernel of the interpolation functions (Eq. 6) by
+ *                        a grid FFT and a dense GEMM over G.
+ *   isdf_fragment_eri    fragment ERIs (Eqs. 17-20, Algorithm 2):
+ *                        (pq|rs) = (1/Nk) sum_q [M^q V^q M^q^H]_{(pq),(sr)} and the
+ *                        Coulomb / exchange energy traces.
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are interleaved (re, im) doubles (complex128) unless a
+ *     buffer is documented as complex64.  All arrays are row-major in the index
+ *     order written next to them.
+ *   - Grid: mesh n = (n0, n1, n2); point g has r = sum_i g_i/n_i a_i; flat index
+ *     (g0*n1 + g1)*n2 + g2.  N_g = n0 n1 n2.
+ *   - k-mesh: Gamma-centred, unfolded k = sum_i m_i/nk_i b_i, m_i in [0, nk_i),
+ *     flat index (m0*nk1 + m1)*nk2 + m2.  q labels the same mesh.
+ *   - The caller owns every buffer it passes; the handle owns all device
+ *     workspaces (allocated on first use, reused on later calls, freed by
+ *     isdf_destroy).  Device pointers must be on the handle's device.
+ *   - All work is enqueued on the handle's CUDA stream.  A call returns after
+ *     the host-visible outputs it writes are complete; device outputs are
+ *     complete when the stream reaches the end of the call.
+ *   - Every call returns an isdf_status; on failure isdf_last_error() holds a
+ *     message.  No C++ exception crosses this boundary.  A handle is not
+ *     thread-safe.
+ */
+#ifndef ISDF_H
+#define ISDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isdf_handle isdf_handle;
+
+typedef enum {
+  ISDF_OK = 0,
+  ISDF_ERR_ARG = -1,      /* invalid argument (NULL, size, out-of-range value)   */
+  ISDF_ERR_OOM = -2,      /* device allocation failed                             */
+  ISDF_ERR_CUDA = -3,     /* a CUDA runtime call or kernel launch failed          */
+  ISDF_ERR_NUMERIC = -4,  /* non-finite value, or a factorisation found rank 0 /  */
+                          /* the point selection ran out of rank                 */
+  ISDF_ERR_TIMEOUT = -5,  /* a bounded device-side wait expired                   */
+  ISDF_ERR_STATE = -6     /* calls made out of order                              */
+} isdf_status;
+
+typedef enum {
+  ISDF_FP64 = 0,   /* every step in FP64                                          */
+  ISDF_MIXED = 1   /* FP64 fit (Eqs. 3-5); Coulomb GEMM, fragment pair tensor and  */
+                   /* ERI contraction in reduced precision with FP32 accumulation */
+} isdf_precision;
+
+/* Cell, basis and sampling (Eq. 1; Section II).
+ *   lattice     row i = lattice vector a_i in Bohr.
+ *   coords      natm x 3 atom positions in Bohr.
+ *   shells      Cartesian Gaussian shells: shell_atom[s], shell_l[s] (0..4),
+ *               shell_nprim[s]; exps / coefs hold the primitives of all shells
+ *               consecutively (coefs multiply *normalised* primitives).  AO order:
+ *               shells in order, components x^lx y^ly z^lz with lx descending,
+ *               then ly descending (s; x,y,z; xx,xy,xz,yy,yz,zz; ...).
+ *   kmesh, mesh k-mesh and real-space grid per axis.
+ *   lattice_eps lattice-sum truncation: images with alpha_min |r-T|^2 beyond
+ *               -ln(lattice_eps) are dropped (0 selects exp(-40)).
+ * The descriptor is copied by isdf_create; the caller may free it afterwards. */
+typedef struct {
+  double lattice[9];
+  int natm;
+  const double* coords;
+  int nshell;
+  const int* shell_atom;
+  const int* shell_l;
+  const int* shell_nprim;
+  const double* exps;
+  const double* coefs;
+  int kmesh[3];
+  int mesh[3];
+  double lattice_eps;
+} isdf_cell_desc;
+
+/* Create a handle for `cell` computing in `precision`, enqueuing on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream) of the current
+ * device.  Limits: N_AO <= 1024, Nk <= 1024, nk_i <= 16, n_i <= 64. */
+int isdf_create(const isdf_cell_desc* cell, isdf_precision precision, void* cuda_stream,
+                isdf_handle** out);
+
+/* Step S0-S1 (Eq. 1; Section II.A).  Evaluates phi^k_mu(r) on the grid and
+ * selects n_p interpolation points by greedy pivoted Cholesky of the
+ * pair-product Gram K(r,r') = |sum_k sum_mu conj(phi^k_mu(r)) phi^k_mu(r')|^2.
+ * Residual diagonals within 1e-11 * d_max,0 of the largest (and at least half
+ * of it) are ties, broken by the smallest splitmix64(seed ^ r).  Stops with
+ * ISDF_ERR_NUMERIC if the largest residual falls below chol_tol * d_max,0
+ * before n_p points are found.  ip_index_out: host int32[n_p] or NULL. */
+int isdf_build_points(isdf_handle* h, int n_p, uint64_t seed, double chol_tol,
+                      int32_t* ip_index_out);
+
+/* Alternative to the selection: evaluate phi^k_mu(r) and take the n_p given
+ * grid indices (host int32[n_p], each in [0, N_g), distinct) as the
+ * interpolation points. */
+int isdf_set_points(isdf_handle* h, int n_p, const int32_t* ip_index);
+
+/* Step S2 (Eqs. 2-5, Algorithm 1).  Builds Pi^q and eta^q by convolutions over
+ * the k-mesh, factorises Pi^q by pivoted Cholesky with relative truncation
+ * solve_tol (pivot = largest remaining diagonal, ties to the smallest index;
+ * dropped points get zeta = 0) and applies the factor to eta^q.
+ * rank_out: host int32[Nk] (rank of each Pi^q) or NULL. */
+int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out);
+
+/* Step S3 (Eq. 6).  V^q_{IJ} = Omega sum_G conj(c^q_I(G)) c^q_J(G) 4 pi/|q+G|^2
+ * with c^q_I(G) the normalised FFT of e^{-i q.r} zeta^q_I(r) and q+G = 0
+ * dropped.  V_out: device complex128 [Nk][N_P][N_P], or NULL to keep V in the
+ * handle only. */
+int isdf_coulomb_metric(isdf_handle* h, void* V_out);
+
+/* Step S4 (Eqs. 17-20, Algorithm 2).  For each fragment f with n_orb[f]
+ * orbitals phi_p = Nk^{-1/2} sum_k sum_mu C^k_{mu p} phi^k_mu:
+ *   C[f]       device complex128 [Nk][N_AO][n_orb[f]]
+ *   gamma[f]   device complex128 [n_orb][n_orb] Hermitian density matrix with
+ *              density n = sum_pq gamma_pq phi_p^* phi_q; array or entry may be NULL
+ *   eri_out[f] device complex128 [p][q][r][s] chemist's (pq|rs) in FP64 mode,
+ *              complex64 in MIXED mode; array or entry may be NULL
+ *   ej_out[f]  E_J = 1/2 sum gamma_pq gamma_rs (pq|rs)          (host, may be NULL)
+ *   ek_out[f]  E_K = -1/4 sum gamma_ps gamma_rq (pq|rs)         (host, may be NULL)
+ * The traces are accumulated in FP64. */
+int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb,
+                      const void* const* C, const void* const* gamma,
+                      void* const* eri_out, double* ej_out, double* ek_out);
+
+/* Inspection of intermediate results (device outputs, complex128):
+ *   what = 0  X   [Nk][N_P][N_AO]
+ *   what = 1  Pi  [Nk][N_P][N_P]
+ *   what = 2  eta [Nk][N_P][N_g]        (available until isdf_coulomb_metric)
+ *   what = 3  zeta [Nk][N_P][N_g]       (computed on request from the fit)
+ * out must hold the whole array.  Returns ISDF_ERR_STATE if the step that
+ * produces it has not run. */
+int isdf_get(isdf_handle* h, int what, void* out);
+
+/* Sizes: out[0]=N_AO, out[1]=Nk, out[2]=N_g, out[3]=N_P (0 before points). */
+int isdf_sizes(const isdf_handle* h, int64_t* out);
+
+/* Number of kernels this handle has launched since creation. */
+int64_t isdf_launch_count(const isdf_handle* h);
+
+const char* isdf_last_error(const isdf_handle* h);
+void isdf_destroy(isdf_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISDF_H */

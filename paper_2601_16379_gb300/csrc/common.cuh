@@ -1,0 +1,147 @@
+// Internal declarations shared by the CUDA translation units of libisdf.
+// Complex128 is double2 (x = re, y = im); complex64 is float2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+namespace isdf {
+
+// ---------------------------------------------------------------- complex ops
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) {
+  return make_double2(a.x * s, a.y * s);
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// ------------------------------------------------------------- launch errors
+struct Err {
+  int code = 0;
+  std::string msg;
+};
+
+// Counts kernel launches made through the library (for launch accounting).
+extern thread_local int64_t* g_launch_counter;
+inline void count_launch() {
+  if (g_launch_counter) ++*g_launch_counter;
+}
+
+// ------------------------------------------------------------------- kernels
+// Batched complex GEMM, row-major: C_b = alpha * op(A_b) op(B_b) + beta * C_b.
+// op: 'N' as is, 'T' transpose, 'C' conjugate transpose, 'R' conjugate only.
+cudaError_t zgemm(cudaStream_t st, char opA, char opB, int m, int n, int k, double2 alpha,
+                  const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb,
+                  int64_t sB, double2 beta, double2* C, int64_t ldc, int64_t sC, int batch);
+cudaError_t cgemm(cudaStream_t st, char opA, char opB, int m, int n, int k, float2 alpha,
+                  const float2* A, int64_t lda, int64_t sA, const float2* B, int64_t ldb,
+                  int64_t sB, float2 beta, float2* C, int64_t ldc, int64_t sC, int batch);
+
+// k-mesh DFT along the leading (k) axis of data[Nk][ncol] (complex128), in place.
+//   mode 0: data = scale * DFT_s1(data)
+//   mode 1: data = scale * DFT_s2(|DFT_s1(data)|^2)
+// s = +1 means sum_k exp(+2 pi i m.k/nk), s = -1 the opposite sign.
+struct KMesh {
+  int n[3];
+};
+cudaError_t kdft_cols(cudaStream_t st, double2* data, int64_t ncol, KMesh km, int s1, int s2,
+                      int mode, double scale);
+cudaError_t kdft_cols_f(cudaStream_t st, float2* data, int64_t ncol, KMesh km, int s1, int s2,
+                        int mode, float scale);
+
+// Bloch AO values phi[k][mu][r] (complex128).
+struct BasisDev {
+  int nao;
+  int nshell;
+  const int* ao_shell;      // [nao] shell of each AO
+  const int* ao_lxyz;       // [nao*3]
+  const int* sh_atom;       // [nshell]
+  const int* sh_off;        // [nshell+1] primitive offsets
+  const double* prim_exp;   // [nprim]
+  const double* prim_cn;    // [nprim*ncomp?] coef * norm for component 0 (radial)
+  const double* prim_norm;  // [nao * maxprim] coef*norm per AO and primitive
+  const double* coords;     // [natm*3]
+  int maxprim;
+};
+struct CellDev {
+  double lat[9];
+  double rec[9];
+  int kmesh[3];
+  int mesh[3];
+  int lrange[3];
+  double expcut;
+  int orthorhombic;
+};
+cudaError_t ao_eval(cudaStream_t st, const CellDev& c, const BasisDev& b, double2* phi,
+                    double* work1d);
+size_t ao_eval_work_bytes(const CellDev& c, const BasisDev& b);
+
+// IP selection.
+cudaError_t ip_init(cudaStream_t st, const double2* phi, int nkao, int ng, double* d,
+                    double* dscratch);
+cudaError_t ip_step(cudaStream_t st, const double2* phi, int nkao, int ng, int j, double* d,
+                    double* Lt, int32_t* piv, int32_t* chosen, double* partial, int nsplit,
+                    uint64_t seed, double tie_eps, double chol_tol, double* d0, int32_t* status);
+cudaError_t gather_x(cudaStream_t st, const double2* phi, int nk, int nao, int ng,
+                     const int32_t* ips, int np, double2* X);
+
+// Pivoted Cholesky (batched) of Hermitian PSD A[b][n][n].  Lt[b][j][i] = L[i][j].
+cudaError_t pchol_batched(cudaStream_t st, const double2* A, int n, int batch, double tol,
+                          double2* Lt, int32_t* perm, int32_t* rank, double* dwork);
+// Wfull[b] (n x n): Wfull[i][perm[c]] = (L_S^{-1})[i][c], zero elsewhere.
+cudaError_t trinv_batched(cudaStream_t st, const double2* Lt, const int32_t* perm,
+                          const int32_t* rank, int n, int batch, double2* W, double2* work);
+// Lpad[b][i][j] = L[i][j] (row-major, columns beyond the rank zero).
+cudaError_t lt_to_rowmajor(cudaStream_t st, const double2* Lt, const int32_t* rank, int n,
+                           int batch, double2* L);
+
+// Grid FFT of rows x[q][I][r] (complex128), in place:
+//   x <- sqrt(w(q+G)) * (1/N_g) FFT(e^{-i q.r} x)   with w = 4 pi/|q+G|^2, 0 at q+G = 0.
+// dtw: device table of 3 x 64 forward twiddles exp(-2 pi i j/n_a) (grid_twiddles).
+cudaError_t grid_coulomb_fft(cudaStream_t st, double2* x, int rows_per_q, int q0, int nq,
+                             const CellDev& c, const double2* dtw);
+cudaError_t grid_coulomb_fft_f(cudaStream_t st, float2* x, int rows_per_q, int q0, int nq,
+                               const CellDev& c, const double2* dtw);
+void grid_twiddles(const int mesh[3], double2* host192);
+
+// Fragment pair products Z[R][(p q)][I] = conj(t[R][I][p]) * t[R][I][q].
+cudaError_t pair_products(cudaStream_t st, const double2* t, int nk, int np, int nf, double2* Z);
+cudaError_t pair_products_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float2* Z);
+
+// eri[p][q][r][s] = E[(p q)][(s r)] * scale, and the traces.
+cudaError_t eri_permute(cudaStream_t st, const double2* E, int nf, double scale, double2* eri);
+cudaError_t eri_permute_f(cudaStream_t st, const float2* E, int nf, float scale, float2* eri);
+cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale,
+                       const double2* gamma, double* out2);
+cudaError_t eri_traces_f(cudaStream_t st, const float2* E, int nf, double scale,
+                         const double2* gamma, double* out2);
+
+// Precision conversions.
+cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n);
+cudaError_t c2z(cudaStream_t st, const float2* in, double2* out, int64_t n);
+cudaError_t nonfinite_count(cudaStream_t st, const double* x, int64_t n, int32_t* flag);
+
+}  // namespace isdf

@@ -1,0 +1,624 @@
+// C ABI of libisdf: handle, workspaces and the four steps of the k-ISDF
+// fragment-ERI path (Section II of the paper; see include/isdf.h).
+//
+// Step -> kernels
+//   build_points   ao_eval (Eq. 1), ip_init/ip_step (Section II.A), gather_x
+//   fit_zeta       G^k = conj(X^k) X^k^T (zgemm), k-convolution |DFT|^2 -> Pi^q
+//                  (kdft_cols, Eq. 4 / Algorithm 1); g^k = conj(X^k) Phi^k (zgemm),
+//                  k-convolution -> eta^q (Eq. 5); pivoted Cholesky of Pi^q and
+//                  W = L_S^{-1} (Eq. 3); xi^q = W eta^q (zeta^q = W^H xi^q).
+//   coulomb_metric grid FFT of e^{-iq.r} xi^q with sqrt(4 pi/|q+G|^2) (Eq. 6),
+//                  V_xi = Omega c'^* c'^T, V_xi = L_xi L_xi^H, L^q = W^T L_xi so
+//                  that V^q = L^q L^q^H = W^T V_xi conj(W).
+//   fragment_eri   T^k = X^k C^k, t = DFT_k(T), pair products, DFT_R -> M^q
+//                  (Eq. 20 / Algorithm 2); B = [M^q L^q]_q; E = B B^H (Eq. 19);
+//                  chemist's permutation and the J/K traces.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/isdf.h"
+#include "common.cuh"
+
+namespace isdf {
+thread_local int64_t* g_launch_counter = nullptr;
+}
+
+using namespace isdf;
+
+namespace {
+
+constexpr double kTieEps = 1e-11;  // interpolation-point tie window (relative to d_max,0)
+constexpr int kIpSplit = 16;       // column-generation split of the (k, mu) sum
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct isdf_handle {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  isdf_precision prec = ISDF_FP64;
+  CellDev cell{};
+  double volume = 0;
+  int nao = 0, nk = 0, ng = 0, np = 0;
+  // basis (host copies and device arrays)
+  std::vector<int> ao_shell, ao_lxyz, sh_atom, sh_off;
+  std::vector<double> prim_exp, prim_norm, coords;
+  int maxprim = 1;
+  BasisDev bdev{};
+  // owned device buffers by name
+  std::vector<std::pair<std::string, DevBuf>> bufs;
+  bool has_points = false, has_fit = false, has_xi = false, has_coulomb = false;
+  std::vector<int32_t> ips;
+  std::vector<int32_t> ranks;
+  std::string err;
+  int64_t launches = 0;
+
+  void* buf(const char* name) {
+    for (auto& b : bufs)
+      if (b.first == name) return b.second.p;
+    return nullptr;
+  }
+  // Ensure a named device buffer of at least `bytes`; returns nullptr on OOM.
+  void* ensure(const char* name, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    for (auto& b : bufs)
+      if (b.first == name) {
+        if (b.second.bytes >= bytes) return b.second.p;
+        cudaFree(b.second.p);
+        b.second.p = nullptr;
+        b.second.bytes = 0;
+        if (cudaMalloc(&b.second.p, bytes) != cudaSuccess) {
+          cudaGetLastError();
+          return nullptr;
+        }
+        b.second.bytes = bytes;
+        return b.second.p;
+      }
+    DevBuf d;
+    if (cudaMalloc(&d.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    d.bytes = bytes;
+    bufs.emplace_back(name, d);
+    return d.p;
+  }
+  void release(const char* name) {
+    for (auto& b : bufs)
+      if (b.first == name && b.second.p) {
+        cudaFree(b.second.p);
+        b.second.p = nullptr;
+        b.second.bytes = 0;
+      }
+  }
+};
+
+namespace {
+
+struct LaunchScope {
+  int64_t* prev;
+  explicit LaunchScope(isdf_handle* h) : prev(g_launch_counter) { g_launch_counter = &h->launches; }
+  ~LaunchScope() { g_launch_counter = prev; }
+};
+
+int fail(isdf_handle* h, int code, const char* fmt, ...) {
+  char b[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b, sizeof(b), fmt, ap);
+  va_end(ap);
+  if (h) h->err = b;
+  return code;
+}
+
+#define CK(expr)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(h, ISDF_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),      \
+                  __FILE__, __LINE__);                                                             \
+  } while (0)
+
+#define ENSURE(var, type, name, count)                                                             \
+  type* var = static_cast<type*>(h->ensure(name, sizeof(type) * (size_t)(count)));                 \
+  if (!var) return fail(h, ISDF_ERR_OOM, "device allocation of %s (%zu bytes) failed", name,      \
+                        sizeof(type) * (size_t)(count));
+
+double dfact(int n) {
+  double r = 1.0;
+  while (n > 1) {
+    r *= n;
+    n -= 2;
+  }
+  return r;
+}
+
+double prim_norm(double a, int lx, int ly, int lz) {
+  const int l = lx + ly + lz;
+  const double n2 = std::pow(2.0 * a / M_PI, 1.5) * std::pow(4.0 * a, l) /
+                    (dfact(2 * lx - 1) * dfact(2 * ly - 1) * dfact(2 * lz - 1));
+  return std::sqrt(n2);
+}
+
+int check_device(isdf_handle* h) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(h, ISDF_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev != h->device)
+    return fail(h, ISDF_ERR_STATE, "current device %d differs from the handle's device %d", dev, h->device);
+  return ISDF_OK;
+}
+
+int upload_basis(isdf_handle* h) {
+  auto up = [&](const char* name, const void* src, size_t bytes) -> void* {
+    void* d = h->ensure(name, bytes);
+    if (!d) return nullptr;
+    if (cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    return d;
+  };
+  BasisDev& b = h->bdev;
+  b.nao = h->nao;
+  b.nshell = (int)h->sh_atom.size();
+  b.maxprim = h->maxprim;
+  b.ao_shell = (const int*)up("ao_shell", h->ao_shell.data(), h->ao_shell.size() * sizeof(int));
+  b.ao_lxyz = (const int*)up("ao_lxyz", h->ao_lxyz.data(), h->ao_lxyz.size() * sizeof(int));
+  b.sh_atom = (const int*)up("sh_atom", h->sh_atom.data(), h->sh_atom.size() * sizeof(int));
+  b.sh_off = (const int*)up("sh_off", h->sh_off.data(), h->sh_off.size() * sizeof(int));
+  b.prim_exp = (const double*)up("prim_exp", h->prim_exp.data(), h->prim_exp.size() * sizeof(double));
+  b.prim_norm = (const double*)up("prim_norm", h->prim_norm.data(), h->prim_norm.size() * sizeof(double));
+  b.coords = (const double*)up("coords", h->coords.data(), h->coords.size() * sizeof(double));
+  b.prim_cn = nullptr;
+  if (!b.ao_shell || !b.ao_lxyz || !b.sh_atom || !b.sh_off || !b.prim_exp || !b.prim_norm || !b.coords)
+    return fail(h, ISDF_ERR_OOM, "uploading the basis failed");
+  double2 tw[192];
+  grid_twiddles(h->cell.mesh, tw);
+  if (!up("grid_tw", tw, sizeof(tw))) return fail(h, ISDF_ERR_OOM, "uploading twiddles failed");
+  return ISDF_OK;
+}
+
+// Evaluate Phi into the handle (all precisions keep Phi in FP64).
+int eval_phi(isdf_handle* h) {
+  ENSURE(phi, double2, "phi", (size_t)h->nk * h->nao * h->ng);
+  ENSURE(work, double, "ao_work", ao_eval_work_bytes(h->cell, h->bdev) / sizeof(double) + 2);
+  CK(ao_eval(h->st, h->cell, h->bdev, phi, work));
+  return ISDF_OK;
+}
+
+int finish_points(isdf_handle* h) {
+  const int np = h->np;
+  double2* phi = (double2*)h->buf("phi");
+  int32_t* ipsd = (int32_t*)h->buf("ips");
+  ENSURE(X, double2, "X", (size_t)h->nk * np * h->nao);
+  CK(gather_x(h->st, phi, h->nk, h->nao, h->ng, ipsd, np, X));
+  h->has_points = true;
+  h->has_fit = h->has_xi = h->has_coulomb = false;
+  return ISDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int isdf_create(const isdf_cell_desc* c, isdf_precision precision, void* cuda_stream, isdf_handle** out) {
+  if (!out) return ISDF_ERR_ARG;
+  *out = nullptr;
+  if (!c) return ISDF_ERR_ARG;
+  if (precision != ISDF_FP64 && precision != ISDF_MIXED) return ISDF_ERR_ARG;
+  if (c->natm < 1 || c->nshell < 1 || !c->coords || !c->shell_atom || !c->shell_l || !c->shell_nprim ||
+      !c->exps || !c->coefs)
+    return ISDF_ERR_ARG;
+  int64_t nk = 1, ng = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (c->kmesh[a] < 1 || c->kmesh[a] > 16 || c->mesh[a] < 1 || c->mesh[a] > 64) return ISDF_ERR_ARG;
+    nk *= c->kmesh[a];
+    ng *= c->mesh[a];
+  }
+  if (nk > 1024) return ISDF_ERR_ARG;
+  isdf_handle* h = new isdf_handle();
+  h->prec = precision;
+  h->st = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return ISDF_ERR_CUDA;
+  }
+  // basis
+  int nao = 0, poff = 0, maxprim = 1;
+  for (int s = 0; s < c->nshell; ++s) {
+    const int l = c->shell_l[s], npr = c->shell_nprim[s], at = c->shell_atom[s];
+    if (l < 0 || l > 4 || npr < 1 || at < 0 || at >= c->natm) {
+      delete h;
+      return ISDF_ERR_ARG;
+    }
+    for (int p = 0; p < npr; ++p)
+      if (!(c->exps[poff + p] > 0.0) || !std::isfinite(c->coefs[poff + p])) {
+        delete h;
+        return ISDF_ERR_ARG;
+      }
+    maxprim = std::max(maxprim, npr);
+    h->sh_atom.push_back(at);
+    h->sh_off.push_back(poff);
+    for (int p = 0; p < npr; ++p) h->prim_exp.push_back(c->exps[poff + p]);
+    poff += npr;
+    nao += (l + 1) * (l + 2) / 2;
+  }
+  h->sh_off.push_back(poff);
+  if (nao > 1024) {
+    delete h;
+    return ISDF_ERR_ARG;
+  }
+  h->maxprim = maxprim;
+  h->prim_norm.assign((size_t)nao * maxprim, 0.0);
+  int mu = 0;
+  for (int s = 0; s < c->nshell; ++s) {
+    const int l = c->shell_l[s];
+    for (int lx = l; lx >= 0; --lx)
+      for (int ly = l - lx; ly >= 0; --ly) {
+        const int lz = l - lx - ly;
+        h->ao_shell.push_back(s);
+        h->ao_lxyz.push_back(lx);
+        h->ao_lxyz.push_back(ly);
+        h->ao_lxyz.push_back(lz);
+        for (int p = 0; p < c->shell_nprim[s]; ++p) {
+          const int gi = h->sh_off[s] + p;
+          h->prim_norm[(size_t)mu * maxprim + p] = c->coefs[gi] * prim_norm(c->exps[gi], lx, ly, lz);
+        }
+        ++mu;
+      }
+  }
+  h->coords.assign(c->coords, c->coords + 3 * c->natm);
+  h->nao = nao;
+  h->nk = (int)nk;
+  h->ng = (int)ng;
+  // cell
+  CellDev& cd = h->cell;
+  std::memcpy(cd.lat, c->lattice, sizeof(cd.lat));
+  const double* A = c->lattice;
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(std::fabs(det) > 0)) {
+    delete h;
+    return ISDF_ERR_ARG;
+  }
+  h->volume = std::fabs(det);
+  // rec = 2 pi inv(A)^T : rows b_i
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) cd.rec[i * 3 + j] = 2.0 * M_PI * inv[j * 3 + i];
+  for (int a = 0; a < 3; ++a) {
+    cd.kmesh[a] = c->kmesh[a];
+    cd.mesh[a] = c->mesh[a];
+  }
+  cd.expcut = (c->lattice_eps > 0.0 && c->lattice_eps < 1.0) ? -std::log(c->lattice_eps) : 40.0;
+  double amin = 1e300;
+  for (double e : h->prim_exp) amin = std::min(amin, e);
+  const double rcut = std::sqrt(cd.expcut / amin);
+  for (int a = 0; a < 3; ++a) {
+    const double bn = std::sqrt(cd.rec[a * 3] * cd.rec[a * 3] + cd.rec[a * 3 + 1] * cd.rec[a * 3 + 1] +
+                                cd.rec[a * 3 + 2] * cd.rec[a * 3 + 2]);
+    cd.lrange[a] = (int)std::ceil(rcut * bn / (2.0 * M_PI)) + 1;
+  }
+  cd.orthorhombic = (A[1] == 0 && A[2] == 0 && A[3] == 0 && A[5] == 0 && A[6] == 0 && A[7] == 0) ? 1 : 0;
+  int st = upload_basis(h);
+  if (st != ISDF_OK) {
+    isdf_destroy(h);
+    return st;
+  }
+  *out = h;
+  return ISDF_OK;
+}
+
+int isdf_build_points(isdf_handle* h, int n_p, uint64_t seed, double chol_tol, int32_t* ip_index_out) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (n_p < 1 || n_p > h->ng) return fail(h, ISDF_ERR_ARG, "n_p=%d outside [1, N_g=%d]", n_p, h->ng);
+  if (!(chol_tol >= 0.0)) return fail(h, ISDF_ERR_ARG, "chol_tol must be >= 0");
+  if (int e = eval_phi(h)) return e;
+  const int ng = h->ng, nkao = h->nk * h->nao;
+  double2* phi = (double2*)h->buf("phi");
+  ENSURE(d, double, "ip_d", ng);
+  ENSURE(Lt, double, "ip_Lt", (size_t)n_p * ng);
+  ENSURE(piv, int32_t, "ips", n_p);
+  ENSURE(chosen, int32_t, "ip_chosen", ng);
+  ENSURE(partial, double, "ip_partial", (size_t)kIpSplit * ng);
+  ENSURE(scal, double, "ip_scal", 4);
+  ENSURE(status, int32_t, "ip_status", 1);
+  CK(cudaMemsetAsync(chosen, 0, sizeof(int32_t) * ng, h->st));
+  CK(cudaMemsetAsync(status, 0, sizeof(int32_t), h->st));
+  CK(cudaMemsetAsync(piv, 0xff, sizeof(int32_t) * n_p, h->st));
+  CK(ip_init(h->st, phi, nkao, ng, d, partial));
+  for (int j = 0; j < n_p; ++j)
+    CK(ip_step(h->st, phi, nkao, ng, j, d, Lt, piv, chosen, partial, kIpSplit, seed, kTieEps, chol_tol,
+               scal, status));
+  std::vector<int32_t> hp(n_p);
+  int32_t hs = 0;
+  CK(cudaMemcpyAsync(hp.data(), piv, sizeof(int32_t) * n_p, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (hs != 0) {
+    int found = 0;
+    while (found < n_p && hp[found] >= 0) ++found;
+    h->has_points = false;
+    return fail(h, ISDF_ERR_NUMERIC, "pivoted Cholesky stopped after %d of %d points (residual below tolerance)",
+                found, n_p);
+  }
+  h->np = n_p;
+  h->ips = hp;
+  if (ip_index_out) std::memcpy(ip_index_out, hp.data(), sizeof(int32_t) * n_p);
+  return finish_points(h);
+}
+
+int isdf_set_points(isdf_handle* h, int n_p, const int32_t* ip_index) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!ip_index || n_p < 1 || n_p > h->ng) return fail(h, ISDF_ERR_ARG, "invalid interpolation points");
+  std::vector<char> seen(h->ng, 0);
+  for (int i = 0; i < n_p; ++i) {
+    if (ip_index[i] < 0 || ip_index[i] >= h->ng || seen[ip_index[i]])
+      return fail(h, ISDF_ERR_ARG, "point %d (%d) out of range or repeated", i, ip_index[i]);
+    seen[ip_index[i]] = 1;
+  }
+  if (int e = eval_phi(h)) return e;
+  ENSURE(piv, int32_t, "ips", n_p);
+  CK(cudaMemcpyAsync(piv, ip_index, sizeof(int32_t) * n_p, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->np = n_p;
+  h->ips.assign(ip_index, ip_index + n_p);
+  return finish_points(h);
+}
+
+int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!h->has_points) return fail(h, ISDF_ERR_STATE, "isdf_fit_zeta before the interpolation points");
+  if (!(solve_tol >= 0.0) || !(solve_tol < 1.0)) return fail(h, ISDF_ERR_ARG, "solve_tol must be in [0, 1)");
+  const int nk = h->nk, np = h->np, nao = h->nao, ng = h->ng;
+  const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
+  double2* X = (double2*)h->buf("X");
+  double2* phi = (double2*)h->buf("phi");
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  // Pi^q (Eq. 4): G^k_IJ = sum_mu conj(X^k_I mu) X^k_J mu, then the k-convolution
+  ENSURE(Pi, double2, "Pi", (size_t)nk * np * np);
+  CK(zgemm(h->st, 'R', 'T', np, np, nao, one, X, nao, (int64_t)np * nao, X, nao, (int64_t)np * nao, zero, Pi,
+           np, (int64_t)np * np, nk));
+  CK(kdft_cols(h->st, Pi, (int64_t)np * np, km, +1, -1, 1, 1.0 / nk));
+  // eta^q (Eq. 5): g^k_I(r) = sum_mu conj(X^k_I mu) Phi^k_mu(r), then the k-convolution
+  ENSURE(eta, double2, "eta", (size_t)nk * np * ng);
+  CK(zgemm(h->st, 'R', 'N', np, ng, nao, one, X, nao, (int64_t)np * nao, phi, ng, (int64_t)nao * ng, zero, eta,
+           ng, (int64_t)np * ng, nk));
+  CK(kdft_cols(h->st, eta, (int64_t)np * ng, km, +1, -1, 1, 1.0 / nk));
+  // Pi^q = L L^H (pivoted), W = L_S^{-1}
+  ENSURE(LtPi, double2, "LtPi", (size_t)nk * np * np);
+  ENSURE(permPi, int32_t, "permPi", (size_t)nk * np);
+  ENSURE(rankPi, int32_t, "rankPi", nk);
+  ENSURE(dwork, double, "chol_dwork", (size_t)nk * 2 * np);
+  CK(pchol_batched(h->st, Pi, np, nk, solve_tol, LtPi, permPi, rankPi, dwork));
+  ENSURE(W, double2, "W", (size_t)nk * np * np);
+  ENSURE(wwork, double2, "W_work", (size_t)nk * np * np);
+  CK(trinv_batched(h->st, LtPi, permPi, rankPi, np, nk, W, wwork));
+  // xi^q = W eta^q
+  ENSURE(xi, double2, "xi", (size_t)nk * np * ng);
+  CK(zgemm(h->st, 'N', 'N', np, ng, np, one, W, np, (int64_t)np * np, eta, ng, (int64_t)np * ng, zero, xi, ng,
+           (int64_t)np * ng, nk));
+  h->ranks.assign(nk, 0);
+  CK(cudaMemcpyAsync(h->ranks.data(), rankPi, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (rank_out) std::memcpy(rank_out, h->ranks.data(), sizeof(int32_t) * nk);
+  for (int q = 0; q < nk; ++q)
+    if (h->ranks[q] < 1) return fail(h, ISDF_ERR_NUMERIC, "Pi^q has rank 0 at q=%d", q);
+  h->has_fit = true;
+  h->has_xi = true;
+  h->has_coulomb = false;
+  return ISDF_OK;
+}
+
+int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!h->has_fit || !h->has_xi) return fail(h, ISDF_ERR_STATE, "isdf_coulomb_metric before isdf_fit_zeta");
+  const int nk = h->nk, np = h->np, ng = h->ng;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  double2* xi = (double2*)h->buf("xi");
+  double2* W = (double2*)h->buf("W");
+  const double2* tw = (const double2*)h->buf("grid_tw");
+  ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
+  if (h->prec == ISDF_FP64) {
+    CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw));
+    CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi, ng, (int64_t)np * ng, xi, ng,
+             (int64_t)np * ng, zero, Vxi, np, (int64_t)np * np, nk));
+  } else {
+    ENSURE(xif, float2, "xi_f", (size_t)nk * np * ng);
+    ENSURE(Vxif, float2, "Vxi_f", (size_t)nk * np * np);
+    CK(z2c(h->st, xi, xif, (int64_t)nk * np * ng));
+    CK(grid_coulomb_fft_f(h->st, xif, np, 0, nk, h->cell, tw));
+    CK(cgemm(h->st, 'R', 'T', np, np, ng, make_float2((float)h->volume, 0.f), xif, ng, (int64_t)np * ng, xif,
+             ng, (int64_t)np * ng, make_float2(0.f, 0.f), Vxif, np, (int64_t)np * np, nk));
+    CK(c2z(h->st, Vxif, Vxi, (int64_t)nk * np * np));
+  }
+  h->has_xi = false;  // xi was transformed in place (FP64) / is no longer needed
+  // V_xi = L_xi L_xi^H ; L^q = W^T L_xi
+  ENSURE(LtV, double2, "LtV", (size_t)nk * np * np);
+  ENSURE(permV, int32_t, "permV", (size_t)nk * np);
+  ENSURE(rankV, int32_t, "rankV", nk);
+  ENSURE(dwork, double, "chol_dwork", (size_t)nk * 2 * np);
+  CK(pchol_batched(h->st, Vxi, np, nk, 1e-15, LtV, permV, rankV, dwork));
+  ENSURE(Lxi, double2, "W_work", (size_t)nk * np * np);
+  CK(lt_to_rowmajor(h->st, LtV, rankV, np, nk, Lxi));
+  ENSURE(Lq, double2, "Lq", (size_t)nk * np * np);
+  CK(zgemm(h->st, 'T', 'N', np, np, np, one, W, np, (int64_t)np * np, Lxi, np, (int64_t)np * np, zero, Lq, np,
+           (int64_t)np * np, nk));
+  if (V_out) {
+    // V^q = W^T V_xi conj(W)
+    double2* tmp = Lxi;  // reuse
+    CK(zgemm(h->st, 'N', 'R', np, np, np, one, Vxi, np, (int64_t)np * np, W, np, (int64_t)np * np, zero, tmp, np,
+             (int64_t)np * np, nk));
+    CK(zgemm(h->st, 'T', 'N', np, np, np, one, W, np, (int64_t)np * np, tmp, np, (int64_t)np * np, zero,
+             (double2*)V_out, np, (int64_t)np * np, nk));
+  }
+  if (h->prec == ISDF_MIXED) {
+    ENSURE(Lqf, float2, "Lq_f", (size_t)nk * np * np);
+    CK(z2c(h->st, Lq, Lqf, (int64_t)nk * np * np));
+    ENSURE(Xf, float2, "X_f", (size_t)nk * np * h->nao);
+    CK(z2c(h->st, (const double2*)h->buf("X"), Xf, (int64_t)nk * np * h->nao));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  h->has_coulomb = true;
+  return ISDF_OK;
+}
+
+int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const void* const* C,
+                      const void* const* gamma, void* const* eri_out, double* ej_out, double* ek_out) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!h->has_coulomb) return fail(h, ISDF_ERR_STATE, "isdf_fragment_eri before isdf_coulomb_metric");
+  if (n_frag < 0 || (n_frag > 0 && (!n_orb || !C))) return fail(h, ISDF_ERR_ARG, "invalid fragment arrays");
+  const int nk = h->nk, np = h->np, nao = h->nao;
+  const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
+  const bool mixed = (h->prec == ISDF_MIXED);
+  for (int f = 0; f < n_frag; ++f) {
+    const int nf = n_orb[f];
+    if (nf < 1 || nf > 4096 || !C[f]) return fail(h, ISDF_ERR_ARG, "fragment %d: bad size or NULL C", f);
+    if ((int64_t)nf * nf > 65535LL * 64) return fail(h, ISDF_ERR_ARG, "fragment %d too large", f);
+  }
+  for (int f = 0; f < n_frag; ++f) {
+    const int nf = n_orb[f];
+    const int64_t n2 = (int64_t)nf * nf;
+    const double2* Cf = (const double2*)C[f];
+    double* trf = nullptr;
+    const bool want_tr = (ej_out || ek_out) && gamma && gamma[f];
+    if (want_tr) {
+      trf = (double*)h->ensure("traces", sizeof(double) * (8 + 4 * (size_t)n2));
+      if (!trf) return fail(h, ISDF_ERR_OOM, "traces workspace");
+    }
+    if (!mixed) {
+      const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+      double2* X = (double2*)h->buf("X");
+      double2* Lq = (double2*)h->buf("Lq");
+      ENSURE(T, double2, "frag_T", (size_t)nk * np * nf);
+      CK(zgemm(h->st, 'N', 'N', np, nf, nao, one, X, nao, (int64_t)np * nao, Cf, nf, (int64_t)nao * nf, zero, T,
+               nf, (int64_t)np * nf, nk));
+      CK(kdft_cols(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.0));
+      ENSURE(M, double2, "frag_M", (size_t)nk * n2 * np);
+      CK(pair_products(h->st, T, nk, np, nf, M));
+      CK(kdft_cols(h->st, M, n2 * np, km, +1, +1, 0, 1.0 / nk));
+      ENSURE(B, double2, "frag_B", (size_t)n2 * nk * np);
+      CK(zgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lq, np, (int64_t)np * np, zero, B,
+               (int64_t)nk * np, np, nk));
+      ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
+      CK(zgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0, zero,
+               E, n2, 0, 1));
+      if (eri_out && eri_out[f]) CK(eri_permute(h->st, E, nf, 1.0 / nk, (double2*)eri_out[f]));
+      if (want_tr) CK(eri_traces(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf));
+    } else {
+      const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+      float2* Xf = (float2*)h->buf("X_f");
+      float2* Lqf = (float2*)h->buf("Lq_f");
+      ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nf);
+      CK(z2c(h->st, Cf, Cff, (int64_t)nk * nao * nf));
+      ENSURE(T, float2, "frag_Tf", (size_t)nk * np * nf);
+      CK(cgemm(h->st, 'N', 'N', np, nf, nao, one, Xf, nao, (int64_t)np * nao, Cff, nf, (int64_t)nao * nf, zero, T,
+               nf, (int64_t)np * nf, nk));
+      CK(kdft_cols_f(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.f));
+      ENSURE(M, float2, "frag_Mf", (size_t)nk * n2 * np);
+      CK(pair_products_f(h->st, T, nk, np, nf, M));
+      CK(kdft_cols_f(h->st, M, n2 * np, km, +1, +1, 0, 1.f / nk));
+      ENSURE(B, float2, "frag_Bf", (size_t)n2 * nk * np);
+      CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lqf, np, (int64_t)np * np, zero, B,
+               (int64_t)nk * np, np, nk));
+      ENSURE(E, float2, "frag_Ef", (size_t)n2 * n2);
+      CK(cgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0, zero,
+               E, n2, 0, 1));
+      if (eri_out && eri_out[f]) CK(eri_permute_f(h->st, E, nf, 1.f / nk, (float2*)eri_out[f]));
+      if (want_tr) CK(eri_traces_f(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf));
+    }
+    if (want_tr) {
+      double hv[4];
+      CK(cudaMemcpyAsync(hv, trf, sizeof(hv), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      if (ej_out) ej_out[f] = hv[0];
+      if (ek_out) ek_out[f] = hv[1];
+    } else {
+      if (ej_out) ej_out[f] = 0.0;
+      if (ek_out) ek_out[f] = 0.0;
+    }
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return ISDF_OK;
+}
+
+int isdf_get(isdf_handle* h, int what, void* out) {
+  if (!h || !out) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  const int nk = h->nk, np = h->np, ng = h->ng, nao = h->nao;
+  switch (what) {
+    case 0:
+      if (!h->has_points) return fail(h, ISDF_ERR_STATE, "X not available");
+      CK(cudaMemcpyAsync(out, h->buf("X"), sizeof(double2) * (size_t)nk * np * nao, cudaMemcpyDeviceToDevice, h->st));
+      break;
+    case 1:
+      if (!h->has_fit) return fail(h, ISDF_ERR_STATE, "Pi not available");
+      CK(cudaMemcpyAsync(out, h->buf("Pi"), sizeof(double2) * (size_t)nk * np * np, cudaMemcpyDeviceToDevice, h->st));
+      break;
+    case 2:
+      if (!h->has_fit) return fail(h, ISDF_ERR_STATE, "eta not available");
+      CK(cudaMemcpyAsync(out, h->buf("eta"), sizeof(double2) * (size_t)nk * np * ng, cudaMemcpyDeviceToDevice, h->st));
+      break;
+    case 3: {
+      if (!h->has_xi) return fail(h, ISDF_ERR_STATE, "zeta not available (needs isdf_fit_zeta, before the metric)");
+      const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+      CK(zgemm(h->st, 'C', 'N', np, ng, np, one, (double2*)h->buf("W"), np, (int64_t)np * np, (double2*)h->buf("xi"),
+               ng, (int64_t)np * ng, zero, (double2*)out, ng, (int64_t)np * ng, nk));
+      break;
+    }
+    default:
+      return fail(h, ISDF_ERR_ARG, "unknown item %d", what);
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return ISDF_OK;
+}
+
+int isdf_sizes(const isdf_handle* h, int64_t* out) {
+  if (!h || !out) return ISDF_ERR_ARG;
+  out[0] = h->nao;
+  out[1] = h->nk;
+  out[2] = h->ng;
+  out[3] = h->has_points ? h->np : 0;
+  return ISDF_OK;
+}
+
+int64_t isdf_launch_count(const isdf_handle* h) { return h ? h->launches : 0; }
+
+const char* isdf_last_error(const isdf_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void isdf_destroy(isdf_handle* h) {
+  if (!h) return;
+  for (auto& b : h->bufs)
+    if (b.second.p) cudaFree(b.second.p);
+  delete h;
+}
+
+}  // extern "C"

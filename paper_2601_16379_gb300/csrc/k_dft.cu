@@ -1,0 +1,377 @@
+// Small DFTs of the k-ISDF path.
+//
+// kdft_cols      transforms along the k-mesh for many independent columns: the
+//                convolution theorem of Algorithm 1 (Pi^q, eta^q: k -> R, |.|^2,
+//                R -> q) and Algorithm 2 (T^k -> T^R, pair products, R -> q).
+// grid_coulomb   cell-grid FFT of e^{-iq.r} x(r) with the 4 pi/|q+G|^2 weight
+//                (Eq. 6), producing sqrt(w) c(G) so that V = Omega c'^H c'.
+// pair_products  the outer product of Algorithm 2 in supercell space.
+//
+// All transforms are direct per-axis DFTs staged through shared memory (mesh
+// axes are at most 16 points for the k-mesh and 64 for the grid), with the
+// twiddles exp(+-2 pi i j/n) tabulated on the host.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace isdf {
+
+namespace {
+
+template <typename T>
+struct CT {};
+template <>
+struct CT<double2> {
+  using R = double;
+  __device__ static double2 mk(double a, double b) { return make_double2(a, b); }
+};
+template <>
+struct CT<float2> {
+  using R = float;
+  __device__ static float2 mk(float a, float b) { return make_float2(a, b); }
+};
+
+struct Twiddles16 {
+  double c[3][16];
+  double s[3][16];
+};
+
+Twiddles16 make_tw(const int n[3], int sign) {
+  Twiddles16 t;
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 16; ++j) {
+      double ang = (n[a] > 0 && j < n[a]) ? 2.0 * M_PI * (double)j / (double)n[a] : 0.0;
+      t.c[a][j] = std::cos(ang);
+      t.s[a][j] = sign * std::sin(ang);
+    }
+  return t;
+}
+
+// In-place DFT along the three k-mesh axes of s[k][c] (Nk x ct), line per thread.
+template <typename T>
+__device__ void kmesh_dft_smem(T* s, int ct, const int n[3], const Twiddles16& tw) {
+  using R = typename CT<T>::R;
+  const int nk = n[0] * n[1] * n[2];
+  for (int a = 2; a >= 0; --a) {
+    const int L = n[a];
+    if (L == 1) continue;
+    const int stride = (a == 2) ? 1 : (a == 1 ? n[2] : n[1] * n[2]);
+    const int nlines = (nk / L) * ct;
+    for (int line = threadIdx.x; line < nlines; line += blockDim.x) {
+      const int c = line % ct;
+      const int rest = line / ct;  // index over the other two axes
+      // base k index with m_a = 0
+      const int hi = rest / stride, lo = rest % stride;
+      const int base = hi * stride * L + lo;
+      T v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (i < L) v[i] = s[(base + i * stride) * ct + c];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j >= L) break;
+        R ax = 0, ay = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (i >= L) break;
+          const int t = (i * j) % L;
+          const R cr = (R)tw.c[a][t], ci = (R)tw.s[a][t];
+          ax += v[i].x * cr - v[i].y * ci;
+          ay += v[i].x * ci + v[i].y * cr;
+        }
+        s[(base + j * stride) * ct + c] = CT<T>::mk(ax, ay);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kdft_cols_kernel(T* __restrict__ data, int64_t ncol, KMesh km,
+                                                        int ct, int mode, Twiddles16 tw1,
+                                                        Twiddles16 tw2, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int nk = km.n[0] * km.n[1] * km.n[2];
+  const int64_t c0 = (int64_t)blockIdx.x * ct;
+  for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+    const int k = e / ct, c = e % ct;
+    const int64_t col = c0 + c;
+    T v = CT<T>::mk(0, 0);
+    if (col < ncol) v = data[(int64_t)k * ncol + col];
+    s[e] = v;
+  }
+  __syncthreads();
+  kmesh_dft_smem<T>(s, ct, km.n, tw1);
+  if (mode == 1) {
+    for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+      T v = s[e];
+      s[e] = CT<T>::mk(v.x * v.x + v.y * v.y, 0);
+    }
+    __syncthreads();
+    kmesh_dft_smem<T>(s, ct, km.n, tw2);
+  }
+  using R = typename CT<T>::R;
+  for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+    const int k = e / ct, c = e % ct;
+    const int64_t col = c0 + c;
+    if (col < ncol) {
+      T v = s[e];
+      data[(int64_t)k * ncol + col] = CT<T>::mk(v.x * (R)scale, v.y * (R)scale);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t kdft_launch(cudaStream_t st, T* data, int64_t ncol, KMesh km, int s1, int s2, int mode,
+                        double scale) {
+  const int nk = km.n[0] * km.n[1] * km.n[2];
+  for (int a = 0; a < 3; ++a)
+    if (km.n[a] < 1 || km.n[a] > 16) return cudaErrorInvalidValue;
+  if (ncol <= 0) return cudaSuccess;
+  int ct = (int)(65536 / ((int64_t)nk * sizeof(T)));
+  if (ct < 1) ct = 1;
+  if (ct > 32) ct = 32;
+  size_t smem = (size_t)nk * ct * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kdft_cols_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int64_t nblk = (ncol + ct - 1) / ct;
+  if (nblk > 2147483647LL) return cudaErrorInvalidValue;
+  kdft_cols_kernel<T><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, km, ct, mode,
+                                                         make_tw(km.n, s1), make_tw(km.n, s2), scale);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ grid FFT
+struct GridFFTParams {
+  int n[3];
+  int kmesh[3];
+  double rec[9];
+};
+
+// x[row][r] *= exp(-i q.r), q = sum_a m_a/nk_a b_a  (rows grouped by q)
+template <typename T>
+__global__ void phase_kernel(T* __restrict__ x, int64_t rows_per_q, int q0, int nq,
+                             GridFFTParams p) {
+  using R = typename CT<T>::R;
+  const int ng = p.n[0] * p.n[1] * p.n[2];
+  const int64_t total = (int64_t)nq * rows_per_q * ng;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % ng);
+    const int qi = (int)(e / ((int64_t)rows_per_q * ng));
+    const int q = q0 + qi;
+    const int m2 = q % p.kmesh[2], m1 = (q / p.kmesh[2]) % p.kmesh[1], m0 = q / (p.kmesh[1] * p.kmesh[2]);
+    const int g2 = r % p.n[2], g1 = (r / p.n[2]) % p.n[1], g0 = r / (p.n[1] * p.n[2]);
+    // fraction of a full turn, reduced exactly per axis
+    const double f = (double)((m0 * g0) % (p.kmesh[0] * p.n[0])) / (double)(p.kmesh[0] * p.n[0]) +
+                     (double)((m1 * g1) % (p.kmesh[1] * p.n[1])) / (double)(p.kmesh[1] * p.n[1]) +
+                     (double)((m2 * g2) % (p.kmesh[2] * p.n[2])) / (double)(p.kmesh[2] * p.n[2]);
+    double sn, cs;
+    sincospi(-2.0 * (f - floor(f)), &sn, &cs);
+    T v = x[e];
+    x[e] = CT<T>::mk(v.x * (R)cs - v.y * (R)sn, v.x * (R)sn + v.y * (R)cs);
+  }
+}
+
+// One axis of the forward grid DFT, lines of length L with element stride S.
+// Block: lpb lines x L outputs; smem holds the lines.
+template <typename T>
+__global__ void __launch_bounds__(256) grid_axis_kernel(T* __restrict__ x, int64_t nrows, int ng,
+                                                        int L, int64_t S, int lpb,
+                                                        const double2* __restrict__ tw) {
+  using R = typename CT<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tws = reinterpret_cast<double2*>(smem_raw);  // 64 entries, 16-byte aligned
+  T* s = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double2));
+  const int64_t lines_per_row = ng / L;
+  const int64_t total_lines = nrows * lines_per_row;
+  const int64_t l0 = (int64_t)blockIdx.x * lpb;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = tw[t];
+  // line id -> base element offset
+  auto base_of = [&](int64_t line) -> int64_t {
+    const int64_t row = line / lines_per_row;
+    const int64_t lr = line % lines_per_row;  // index over the other axes
+    const int64_t hi = lr / S, lo = lr % S;
+    return row * ng + hi * S * L + lo;
+  };
+  for (int e = threadIdx.x; e < lpb * L; e += blockDim.x) {
+    int li, i;
+    if (S == 1) {
+      li = e / L;
+      i = e % L;
+    } else {
+      li = e % lpb;
+      i = e / lpb;
+    }
+    const int64_t line = l0 + li;
+    T v = CT<T>::mk(0, 0);
+    if (line < total_lines) v = x[base_of(line) + (int64_t)i * S];
+    s[li * L + i] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < lpb * L; e += blockDim.x) {
+    int li, j;
+    if (S == 1) {
+      li = e / L;
+      j = e % L;
+    } else {
+      li = e % lpb;
+      j = e / lpb;
+    }
+    const int64_t line = l0 + li;
+    if (line >= total_lines) continue;
+    const T* sl = s + li * L;
+    R ax = 0, ay = 0;
+    int t = 0;
+    for (int i = 0; i < L; ++i) {
+      const double2 w = tws[t];
+      const T v = sl[i];
+      ax += v.x * (R)w.x - v.y * (R)w.y;
+      ay += v.x * (R)w.y + v.y * (R)w.x;
+      t += j;
+      if (t >= L) t -= L;
+      if (t >= L) t %= L;
+    }
+    x[base_of(line) + (int64_t)j * S] = CT<T>::mk(ax, ay);
+  }
+}
+
+// x[row][G] *= sqrt(w(q+G)) / N_g
+template <typename T>
+__global__ void coulomb_weight_kernel(T* __restrict__ x, int64_t rows_per_q, int q0, int nq,
+                                      GridFFTParams p) {
+  using R = typename CT<T>::R;
+  const int ng = p.n[0] * p.n[1] * p.n[2];
+  const int64_t total = (int64_t)nq * rows_per_q * ng;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(e % ng);
+    const int q = q0 + (int)(e / ((int64_t)rows_per_q * ng));
+    const int m2 = q % p.kmesh[2], m1 = (q / p.kmesh[2]) % p.kmesh[1], m0 = q / (p.kmesh[1] * p.kmesh[2]);
+    const int h2 = h % p.n[2], h1 = (h / p.n[2]) % p.n[1], h0 = h / (p.n[1] * p.n[2]);
+    const int hh[3] = {h0, h1, h2};
+    const int mm[3] = {m0, m1, m2};
+    double fr[3];
+    for (int a = 0; a < 3; ++a) {
+      const int gh = (2 * hh[a] < p.n[a]) ? hh[a] : hh[a] - p.n[a];
+      fr[a] = (double)mm[a] / (double)p.kmesh[a] + (double)gh;
+    }
+    double v2 = 0;
+    for (int c = 0; c < 3; ++c) {
+      const double comp = fr[0] * p.rec[0 * 3 + c] + fr[1] * p.rec[1 * 3 + c] + fr[2] * p.rec[2 * 3 + c];
+      v2 += comp * comp;
+    }
+    const bool zero = (mm[0] == 0 && mm[1] == 0 && mm[2] == 0 && fr[0] == 0 && fr[1] == 0 && fr[2] == 0);
+    const double sw = zero ? 0.0 : sqrt(4.0 * M_PI / v2) / (double)ng;
+    T v = x[e];
+    x[e] = CT<T>::mk(v.x * (R)sw, v.y * (R)sw);
+  }
+}
+
+template <typename T>
+cudaError_t grid_fft_launch(cudaStream_t st, T* x, int rows_per_q, int q0, int nq, const CellDev& c,
+                            const double2* dtw) {
+  GridFFTParams p;
+  for (int a = 0; a < 3; ++a) {
+    p.n[a] = c.mesh[a];
+    p.kmesh[a] = c.kmesh[a];
+    if (c.mesh[a] < 1 || c.mesh[a] > 64) return cudaErrorInvalidValue;
+  }
+  for (int i = 0; i < 9; ++i) p.rec[i] = c.rec[i];
+  const int ng = c.mesh[0] * c.mesh[1] * c.mesh[2];
+  const int64_t nrows = (int64_t)rows_per_q * nq;
+  if (nrows == 0) return cudaSuccess;
+  const int64_t total = nrows * ng;
+  int nb = (int)((total + 255) / 256);
+  if (nb > 152 * 64) nb = 152 * 64;
+  phase_kernel<T><<<nb, 256, 0, st>>>(x, rows_per_q, q0, nq, p);
+  count_launch();
+  for (int a = 2; a >= 0; --a) {
+    const int L = c.mesh[a];
+    if (L == 1) continue;
+    const int64_t S = (a == 2) ? 1 : (a == 1 ? c.mesh[2] : (int64_t)c.mesh[1] * c.mesh[2]);
+    int lpb = 256 / L;
+    if (lpb < 1) lpb = 1;
+    const int64_t total_lines = nrows * (ng / L);
+    const int64_t nblk = (total_lines + lpb - 1) / lpb;
+    const size_t smem = (size_t)lpb * L * sizeof(T) + 64 * sizeof(double2);
+    grid_axis_kernel<T><<<(unsigned)nblk, 256, smem, st>>>(x, nrows, ng, L, S, lpb, dtw + a * 64);
+    count_launch();
+  }
+  coulomb_weight_kernel<T><<<nb, 256, 0, st>>>(x, rows_per_q, q0, nq, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void pair_kernel(const T* __restrict__ t, int nk, int np, int nf, T* __restrict__ Z) {
+  const int64_t per = (int64_t)nf * nf * np;
+  const int64_t total = per * nk;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(e % np);
+    const int64_t pq = (e / np) % ((int64_t)nf * nf);
+    const int R = (int)(e / per);
+    const int p = (int)(pq / nf), q = (int)(pq % nf);
+    const T* tr = t + (int64_t)R * np * nf + (int64_t)I * nf;
+    const T a = tr[p], b = tr[q];
+    // conj(a) * b
+    T z;
+    z.x = a.x * b.x + a.y * b.y;
+    z.y = a.x * b.y - a.y * b.x;
+    Z[e] = z;
+  }
+}
+
+}  // namespace
+
+cudaError_t kdft_cols(cudaStream_t st, double2* data, int64_t ncol, KMesh km, int s1, int s2,
+                      int mode, double scale) {
+  return kdft_launch<double2>(st, data, ncol, km, s1, s2, mode, scale);
+}
+cudaError_t kdft_cols_f(cudaStream_t st, float2* data, int64_t ncol, KMesh km, int s1, int s2,
+                        int mode, float scale) {
+  return kdft_launch<float2>(st, data, ncol, km, s1, s2, mode, scale);
+}
+cudaError_t grid_coulomb_fft(cudaStream_t st, double2* x, int rows_per_q, int q0, int nq,
+                             const CellDev& c, const double2* dtw) {
+  return grid_fft_launch<double2>(st, x, rows_per_q, q0, nq, c, dtw);
+}
+cudaError_t grid_coulomb_fft_f(cudaStream_t st, float2* x, int rows_per_q, int q0, int nq,
+                               const CellDev& c, const double2* dtw) {
+  return grid_fft_launch<float2>(st, x, rows_per_q, q0, nq, c, dtw);
+}
+
+void grid_twiddles(const int mesh[3], double2* host192) {
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 64; ++j) {
+      double ang = j < mesh[a] ? 2.0 * M_PI * j / mesh[a] : 0.0;
+      host192[a * 64 + j] = make_double2(std::cos(ang), -std::sin(ang));
+    }
+}
+cudaError_t pair_products(cudaStream_t st, const double2* t, int nk, int np, int nf, double2* Z) {
+  const int64_t total = (int64_t)nk * nf * nf * np;
+  int nb = (int)((total + 255) / 256);
+  if (nb > 152 * 64) nb = 152 * 64;
+  if (total == 0) return cudaSuccess;
+  pair_kernel<double2><<<nb, 256, 0, st>>>(t, nk, np, nf, Z);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t pair_products_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float2* Z) {
+  const int64_t total = (int64_t)nk * nf * nf * np;
+  int nb = (int)((total + 255) / 256);
+  if (nb > 152 * 64) nb = 152 * 64;
+  if (total == 0) return cudaSuccess;
+  pair_kernel<float2><<<nb, 256, 0, st>>>(t, nk, np, nf, Z);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace isdf

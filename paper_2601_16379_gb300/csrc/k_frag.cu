@@ -1,0 +1,169 @@
+// Fragment-ERI epilogues: the chemist's-order permutation of E and the
+// Coulomb / exchange energy traces, plus precision conversions.
+//
+// With E_{(pq),(rs)} = sum_q [M^q V^q M^q^H]_{(pq),(rs)} (scaled by 1/Nk),
+// (pq|rs) = E_{(pq),(sr)}   (Eqs. 19-20 in complex form), and
+//   E_J =  1/2 sum gamma_pq gamma_rs (pq|rs),
+//   E_K = -1/4 sum gamma_ps gamma_rq (pq|rs)   (closed shell, spin-summed gamma).
+// The traces are reduced in FP64 with a fixed order (per-row partials, then a
+// single-block sum), so repeated calls give identical bits.
+#include "common.cuh"
+
+namespace isdf {
+
+namespace {
+
+template <typename T>
+__global__ void eri_permute_kernel(const T* __restrict__ E, int nf, double scale, T* __restrict__ eri) {
+  const int64_t n2 = (int64_t)nf * nf;
+  const int64_t total = n2 * n2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e % nf);
+    const int r = (int)((e / nf) % nf);
+    const int64_t pq = e / n2;
+    T v = E[pq * n2 + (int64_t)s * nf + r];
+    v.x *= scale;
+    v.y *= scale;
+    eri[e] = v;
+  }
+}
+
+// One block per (p q) row: partial J and K sums over (r, s).
+template <typename T>
+__global__ void __launch_bounds__(256) traces_rows_kernel(const T* __restrict__ E, int nf,
+                                                          const double2* __restrict__ g,
+                                                          double2* __restrict__ part) {
+  const int64_t n2 = (int64_t)nf * nf;
+  const int64_t pq = blockIdx.x;
+  const int p = (int)(pq / nf), q = (int)(pq % nf);
+  double2 aj = make_double2(0, 0), ak = make_double2(0, 0);
+  for (int64_t sr = threadIdx.x; sr < n2; sr += blockDim.x) {
+    const int s = (int)(sr / nf), r = (int)(sr % nf);
+    const T ev = E[pq * n2 + sr];  // = (pq|rs)
+    const double2 e2 = make_double2((double)ev.x, (double)ev.y);
+    // J: gamma_rs * (pq|rs)
+    const double2 grs = g[(int64_t)r * nf + s];
+    cfma(aj, grs, e2);
+    // K: gamma_ps gamma_rq (pq|rs)
+    const double2 t = cmul(g[(int64_t)p * nf + s], g[(int64_t)r * nf + q]);
+    cfma(ak, t, e2);
+  }
+  __shared__ double2 sj[256], sk[256];
+  sj[threadIdx.x] = aj;
+  sk[threadIdx.x] = ak;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sj[threadIdx.x] = cadd(sj[threadIdx.x], sj[threadIdx.x + o]);
+      sk[threadIdx.x] = cadd(sk[threadIdx.x], sk[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // J row contribution multiplied by gamma_pq
+    const double2 gpq = g[(int64_t)p * nf + q];
+    part[2 * pq] = cmul(gpq, sj[0]);
+    part[2 * pq + 1] = sk[0];
+  }
+}
+
+__global__ void __launch_bounds__(256) traces_final_kernel(const double2* __restrict__ part, int64_t nrows,
+                                                           double scale, double* __restrict__ out2) {
+  __shared__ double2 sj[256], sk[256];
+  double2 aj = make_double2(0, 0), ak = make_double2(0, 0);
+  for (int64_t i = threadIdx.x; i < nrows; i += blockDim.x) {
+    aj = cadd(aj, part[2 * i]);
+    ak = cadd(ak, part[2 * i + 1]);
+  }
+  sj[threadIdx.x] = aj;
+  sk[threadIdx.x] = ak;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sj[threadIdx.x] = cadd(sj[threadIdx.x], sj[threadIdx.x + o]);
+      sk[threadIdx.x] = cadd(sk[threadIdx.x], sk[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out2[0] = 0.5 * scale * sj[0].x;
+    out2[1] = -0.25 * scale * sk[0].x;
+    out2[2] = 0.5 * scale * sj[0].y;
+    out2[3] = -0.25 * scale * sk[0].y;
+  }
+}
+
+__global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = make_float2((float)in[e].x, (float)in[e].y);
+}
+__global__ void c2z_kernel(const float2* __restrict__ in, double2* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = make_double2((double)in[e].x, (double)in[e].y);
+}
+__global__ void nonfinite_kernel(const double* __restrict__ x, int64_t n, int32_t* __restrict__ flag) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[e])) atomicOr(flag, 1);
+}
+
+inline int nblocks(int64_t total) {
+  int64_t nb = (total + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;
+  return nb < 1 ? 1 : (int)nb;
+}
+
+}  // namespace
+
+cudaError_t eri_permute(cudaStream_t st, const double2* E, int nf, double scale, double2* eri) {
+  eri_permute_kernel<double2><<<nblocks((int64_t)nf * nf * nf * nf), 256, 0, st>>>(E, nf, scale, eri);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t eri_permute_f(cudaStream_t st, const float2* E, int nf, float scale, float2* eri) {
+  eri_permute_kernel<float2><<<nblocks((int64_t)nf * nf * nf * nf), 256, 0, st>>>(E, nf, scale, eri);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// out2 must hold 4 doubles of device memory plus 2*nf*nf double2 of scratch after it
+// (passed as `part`).
+template <typename T>
+static cudaError_t traces_impl(cudaStream_t st, const T* E, int nf, double scale, const double2* gamma,
+                               double* out, double2* part) {
+  const int64_t n2 = (int64_t)nf * nf;
+  traces_rows_kernel<T><<<(unsigned)n2, 256, 0, st>>>(E, nf, gamma, part);
+  count_launch();
+  traces_final_kernel<<<1, 256, 0, st>>>(part, n2, scale, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale, const double2* gamma,
+                       double* out) {
+  double2* part = reinterpret_cast<double2*>(out + 4);
+  return traces_impl<double2>(st, E, nf, scale, gamma, out, part);
+}
+cudaError_t eri_traces_f(cudaStream_t st, const float2* E, int nf, double scale, const double2* gamma,
+                         double* out) {
+  double2* part = reinterpret_cast<double2*>(out + 4);
+  return traces_impl<float2>(st, E, nf, scale, gamma, out, part);
+}
+
+cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n) {
+  z2c_kernel<<<nblocks(n), 256, 0, st>>>(in, out, n);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t c2z(cudaStream_t st, const float2* in, double2* out, int64_t n) {
+  c2z_kernel<<<nblocks(n), 256, 0, st>>>(in, out, n);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t nonfinite_count(cudaStream_t st, const double* x, int64_t n, int32_t* flag) {
+  nonfinite_kernel<<<nblocks(n), 256, 0, st>>>(x, n, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace isdf

@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the FP64 path must match the oracle to 1e-8 Ha in every ERI and in
+E_J / E_K; the mixed path to 1e-6 Ha.  Integer work (interpolation points,
+ranks) must match exactly.  Intermediate arrays of the fit match to ~1e-13
+relative (same FP64 arithmetic in a different order).
+
+The solve tolerance tau of the Pi^q factorisation is part of the problem: the
+basic least-squares solution changes discontinuously when a pivot crosses tau,
+so parity cases use tau values where rounding-level differences cannot move a
+pivot across it (tie windows handle exact symmetry ties).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_16379_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-8
+MIXED_TOL = 1e-6
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_eri(torch, g, frags, prec):
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    Cs = [_dev(torch, f.C) for f in frags]
+    gs = [_dev(torch, f.gamma) for f in frags]
+    outs = [torch.empty((f.norb,) * 4, dtype=dt, device="cuda") for f in frags]
+    ej, ek = g.fragment_eri(Cs, gs, outs)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy().astype(np.complex128) for o in outs], ej, ek
+
+
+class OracleRun:
+    def __init__(self, cell, n_p, seed, ips=None):
+        self.cell = cell
+        self.phi = O.bloch_ao(cell)
+        if ips is None:
+            ips, nf = O.select_ips(self.phi, n_p, seed)
+            assert nf == n_p
+        self.ips = ips
+        self.X = O.interp_vectors(self.phi, ips)
+        self.Pi = O.metric_pi(self.X, cell.kmesh)
+        self.eta = O.rhs_eta(self.X, self.phi, cell.kmesh)
+        self._fits = {}
+
+    def fit(self, tol):
+        if tol not in self._fits:
+            zeta, ranks = O.fit_zeta(self.Pi, self.eta, tol)
+            V = O.coulomb_metric(self.cell, zeta, range(self.cell.nkpts))
+            self._fits[tol] = (zeta, ranks, V)
+        return self._fits[tol]
+
+    def eri(self, tol, f):
+        _, _, V = self.fit(tol)
+        e = O.fragment_eri(self.X, V, f.C, self.cell.kmesh)
+        return e, O.traces(e, f.gamma)
+
+
+def aniso_cell():
+    sh = [W.Shell(0, 0, (0.6,), (1.0,)), W.Shell(1, 1, (0.9,), (1.0,)), W.Shell(1, 2, (1.1,), (0.7,))]
+    return W.custom_cell(5.0, [[0, 0, 0], [0.37, 0.52, 0.21]], sh, (2, 1, 3), (12, 10, 14))
+
+
+@pytest.fixture(scope="module")
+def c1():
+    wl = W.workload("c1")
+    return wl, OracleRun(wl.cell, wl.n_p, wl.seed)
+
+
+@pytest.fixture(scope="module")
+def aniso():
+    cell = aniso_cell()
+    return cell, OracleRun(cell, 40, 99)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    wl = W.workload("c2")
+    return wl, OracleRun(wl.cell, wl.n_p, wl.seed)
+
+
+# ------------------------------------------------------------------ points
+def test_points_bit_exact_c1(cuda, lib_built, c1):
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c1
+    g = B.Isdf(wl.cell, B.ISDF_FP64)
+    assert np.array_equal(g.build_points(wl.n_p, wl.seed), o.ips)
+
+
+def test_points_bit_exact_aniso(cuda, lib_built, aniso):
+    from paper_2601_16379_gb300 import binding as B
+    cell, o = aniso
+    g = B.Isdf(cell, B.ISDF_FP64)
+    assert np.array_equal(g.build_points(40, 99), o.ips)
+
+
+def test_points_c2(cuda, lib_built, c2):
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c2
+    g = B.Isdf(wl.cell, B.ISDF_FP64)
+    assert np.array_equal(g.build_points(wl.n_p, wl.seed), o.ips)
+
+
+# ----------------------------------------------------------- intermediates
+def test_fit_intermediates_c1(cuda, lib_built, c1):
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, o = c1
+    g = B.Isdf(wl.cell, B.ISDF_FP64)
+    g.set_points(o.ips)
+    s = g.sizes()
+    nk, npp, nao, ng = s["nk"], s["np"], s["nao"], s["ng"]
+    X = g.get(0, torch.empty((nk, npp, nao), dtype=torch.complex128, device="cuda")).cpu().numpy()
+    assert np.abs(X - o.X).max() <= 1e-14 * np.abs(o.X).max()
+    ranks = g.fit_zeta(1e-7)
+    assert np.array_equal(ranks, o.fit(1e-7)[1])
+    Pi = g.get(1, torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")).cpu().numpy()
+    assert np.abs(Pi - o.Pi).max() <= 1e-13 * np.abs(o.Pi).max()
+    eta = g.get(2, torch.empty((nk, npp, ng), dtype=torch.complex128, device="cuda")).cpu().numpy()
+    assert np.abs(eta - o.eta).max() <= 1e-13 * np.abs(o.eta).max()
+
+
+def test_zeta_and_V_full_rank(cuda, lib_built, aniso):
+    """Where every Pi^q has full rank the solution is unique: zeta and V match."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    cell, o = aniso
+    tol = 1e-12
+    zeta, ranks, V = o.fit(tol)
+    assert ranks.min() == 40
+    g = B.Isdf(cell, B.ISDF_FP64)
+    g.set_points(o.ips)
+    g.fit_zeta(tol)
+    nk, ng = cell.nkpts, cell.ngrid
+    z = g.get(3, torch.empty((nk, 40, ng), dtype=torch.complex128, device="cuda")).cpu().numpy()
+    assert np.abs(z - zeta).max() <= 1e-5 * np.abs(zeta).max()
+    Vg = torch.empty((nk, 40, 40), dtype=torch.complex128, device="cuda")
+    g.coulomb_metric(Vg)
+    Vg = Vg.cpu().numpy()
+    assert np.abs(Vg - V).max() <= 1e-5 * np.abs(V).max()
+
+
+# ------------------------------------------------------------ fragment ERIs
+@pytest.mark.parametrize("tol", [1e-7])
+def test_fp64_eri_c1(cuda, lib_built, c1, tol):
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c1
+    frags = list(wl.fragments) + [W.make_fragment(wl.cell, wl.seed, 5, 7), W.make_fragment(wl.cell, wl.seed, 6, 1)]
+    g = B.Isdf(wl.cell, B.ISDF_FP64)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(tol)
+    g.coulomb_metric()
+    eris, ej, ek = gpu_eri(cuda, g, frags, 0)
+    for i, f in enumerate(frags):
+        ref, (rj, rk) = o.eri(tol, f)
+        assert np.abs(eris[i] - ref).max() < FP64_TOL
+        assert abs(ej[i] - rj) < FP64_TOL and abs(ek[i] - rk) < FP64_TOL
+
+
+def test_fp64_eri_aniso(cuda, lib_built, aniso):
+    from paper_2601_16379_gb300 import binding as B
+    cell, o = aniso
+    frags = [W.make_fragment(cell, 5, 0, 5), W.make_fragment(cell, 5, 1, 2)]
+    g = B.Isdf(cell, B.ISDF_FP64)
+    g.build_points(40, 99)
+    g.fit_zeta(1e-12)
+    g.coulomb_metric()
+    eris, ej, ek = gpu_eri(cuda, g, frags, 0)
+    for i, f in enumerate(frags):
+        ref, (rj, rk) = o.eri(1e-12, f)
+        assert np.abs(eris[i] - ref).max() < FP64_TOL
+        assert abs(ej[i] - rj) < FP64_TOL and abs(ek[i] - rk) < FP64_TOL
+
+
+def test_mixed_eri_c1(cuda, lib_built, c1):
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c1
+    tol = 1e-7
+    frags = list(wl.fragments) + [W.make_fragment(wl.cell, wl.seed, 5, 7)]
+    g = B.Isdf(wl.cell, B.ISDF_MIXED)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(tol)
+    g.coulomb_metric()
+    eris, ej, ek = gpu_eri(cuda, g, frags, 1)
+    for i, f in enumerate(frags):
+        ref, (rj, rk) = o.eri(tol, f)
+        assert np.abs(eris[i] - ref).max() < MIXED_TOL
+        assert abs(ej[i] - rj) < MIXED_TOL and abs(ek[i] - rk) < MIXED_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7)])
+def test_eri_c2(cuda, lib_built, c2, prec, tol):
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c2
+    g = B.Isdf(wl.cell, prec)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(tol)
+    g.coulomb_metric()
+    eris, ej, ek = gpu_eri(cuda, g, wl.fragments, prec)
+    bound = FP64_TOL if prec == 0 else MIXED_TOL
+    for i, f in enumerate(wl.fragments):
+        ref, (rj, rk) = o.eri(tol, f)
+        assert np.abs(eris[i] - ref).max() < bound
+        assert abs(ej[i] - rj) < bound and abs(ek[i] - rk) < bound
+
+
+# -------------------------------------------------------------- edge cases
+def test_gamma_only_and_general_lattice(cuda, lib_built):
+    """Nk = 1 (textbook Gamma-point ISDF) on a non-orthorhombic (fcc primitive) cell,
+    which takes the direct 3-D lattice-sum kernel."""
+    from paper_2601_16379_gb300 import binding as B
+    a = 6.0
+    lat = 0.5 * a * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    cell = W.Cell(lat, np.array([[0.0, 0.0, 0.0], [0.25 * a, 0.25 * a, 0.25 * a]]),
+                  [W.Shell(0, 0, (0.7,), (1.0,)), W.Shell(1, 1, (1.0,), (1.0,))], (1, 1, 1), (10, 10, 10))
+    for km in ((1, 1, 1), (2, 2, 1)):
+        cell.kmesh = km
+        o = OracleRun(cell, 16, 4)
+        g = B.Isdf(cell, B.ISDF_FP64)
+        assert np.array_equal(g.build_points(16, 4), o.ips)
+        g.fit_zeta(1e-10)
+        g.coulomb_metric()
+        f = W.make_fragment(cell, 9, 0, 3)
+        eris, ej, ek = gpu_eri(cuda, g, [f], 0)
+        ref, (rj, rk) = o.eri(1e-10, f)
+        assert np.abs(eris[0] - ref).max() < FP64_TOL
+        assert abs(ej[0] - rj) < FP64_TOL and abs(ek[0] - rk) < FP64_TOL
+
+
+def test_repeat_is_bitwise_deterministic(cuda, lib_built, c1):
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c1
+    outs = []
+    for _ in range(2):
+        g = B.Isdf(wl.cell, B.ISDF_FP64)
+        g.build_points(wl.n_p, wl.seed)
+        g.fit_zeta(1e-7)
+        g.coulomb_metric()
+        outs.append(gpu_eri(cuda, g, wl.fragments, 0))
+    assert np.array_equal(outs[0][0][0], outs[1][0][0])
+    assert outs[0][1][0] == outs[1][1][0] and outs[0][2][0] == outs[1][2][0]
+
+
+def test_errors_and_state(cuda, lib_built, c1):
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c1
+    g = B.Isdf(wl.cell, B.ISDF_FP64)
+    with pytest.raises(B.IsdfError) as e:
+        g.fit_zeta(1e-7)
+    assert e.value.code == -6
+    with pytest.raises(B.IsdfError) as e:
+        g.coulomb_metric()
+    assert e.value.code == -6
+    with pytest.raises(B.IsdfError) as e:
+        g.build_points(wl.cell.ngrid + 1, 1)
+    assert e.value.code == -1
+    with pytest.raises(B.IsdfError) as e:
+        g.set_points([1, 2, 2])
+    assert e.value.code == -1
+    with pytest.raises(B.IsdfError) as e:
+        g.build_points(4000, wl.seed, chol_tol=1e-2)   # runs out of rank
+    assert e.value.code == -4
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(1e-7)
+    g.coulomb_metric()
+    ej, ek = g.fragment_eri([])
+    assert len(ej) == 0
