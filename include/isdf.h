@@ -60,8 +60,9 @@ typedef enum {
 
 typedef enum {
   ISDF_FP64 = 0,   /* every step in FP64                                          */
-  ISDF_MIXED = 1   /* FP64 fit (Eqs. 3-5); Coulomb GEMM, fragment pair tensor and  */
-                   /* ERI contraction in reduced precision with FP32 accumulation */
+  ISDF_MIXED = 1   /* FP64 points, fit (Eqs. 3-5) and Coulomb metric (Eq. 6); the  */
+                   /* fragment pair tensor and ERI contractions (Eqs. 19-20) in    */
+                   /* reduced precision with compensated FP32 accumulation         */
 } isdf_precision;
 
 /* Cell, basis and sampling (Eq. 1; Section II).
@@ -153,6 +154,18 @@ int isdf_sizes(const isdf_handle* h, int64_t* out);
 
 /* Number of kernels this handle has launched since creation. */
 int64_t isdf_launch_count(const isdf_handle* h);
+
+/* Per-stage device timing with CUDA events recorded on the handle's stream.
+ * isdf_timing_enable(h, 1) clears the totals and starts recording; 0 stops.
+ * isdf_timing_get(h, stage, ...) returns, for
+ *   stage 0  interpolation points (S0-S1)        stage 3  fragment pair tensor M^q (S4a)
+ *   stage 1  fit of zeta (S2)                    stage 4  B^q = M^q L^q (S4b, first half)
+ *   stage 2  Coulomb metric (S3)                 stage 5  E = sum_q B^q B^q^H (S4b, dominant)
+ * the summed device milliseconds, the number of recorded launches of that
+ * stage, and its algorithmic floating-point work (flops) summed over them. */
+int isdf_timing_enable(isdf_handle* h, int enable);
+int isdf_timing_get(const isdf_handle* h, int stage, double* ms_total, int64_t* launches,
+                    double* flops_total);
 
 const char* isdf_last_error(const isdf_handle* h);
 void isdf_destroy(isdf_handle* h);

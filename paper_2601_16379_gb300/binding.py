@@ -25,7 +25,8 @@ STATUS = {0: "ISDF_OK", -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_OOM", -3: "ISDF_ERR_CU
 # Every entry point declared in include/isdf.h.
 EXPORTS = ["isdf_create", "isdf_build_points", "isdf_set_points", "isdf_fit_zeta",
            "isdf_coulomb_metric", "isdf_fragment_eri", "isdf_get", "isdf_sizes",
-           "isdf_launch_count", "isdf_last_error", "isdf_destroy"]
+           "isdf_launch_count", "isdf_timing_enable", "isdf_timing_get", "isdf_last_error",
+           "isdf_destroy"]
 
 
 class IsdfError(RuntimeError):
@@ -65,6 +66,8 @@ def load(path: Optional[str] = None) -> ct.CDLL:
     lib.isdf_sizes.argtypes = [vp, ct.POINTER(ct.c_int64)]
     lib.isdf_launch_count.argtypes = [vp]
     lib.isdf_launch_count.restype = ct.c_int64
+    lib.isdf_timing_enable.argtypes = [vp, ct.c_int]
+    lib.isdf_timing_get.argtypes = [vp, ct.c_int, dp, ct.POINTER(ct.c_int64), dp]
     lib.isdf_last_error.argtypes = [vp]
     lib.isdf_last_error.restype = ct.c_char_p
     lib.isdf_destroy.argtypes = [vp]
@@ -142,6 +145,15 @@ class Isdf:
 
     def launch_count(self) -> int:
         return int(self.lib.isdf_launch_count(self.h))
+
+    def timing(self, enable: bool):
+        self._check(self.lib.isdf_timing_enable(self.h, 1 if enable else 0))
+
+    def stage_time(self, stage: int):
+        """(device ms summed, launches, algorithmic flops summed) of a stage."""
+        ms, n, fl = ct.c_double(), ct.c_int64(), ct.c_double()
+        self._check(self.lib.isdf_timing_get(self.h, int(stage), ct.byref(ms), ct.byref(n), ct.byref(fl)))
+        return ms.value, n.value, fl.value
 
     # -- the four steps ----------------------------------------------------
     def build_points(self, n_p: int, seed: int, chol_tol: float = 1e-14) -> np.ndarray:

@@ -62,6 +62,43 @@ struct isdf_handle {
   std::vector<int32_t> ranks;
   std::string err;
   int64_t launches = 0;
+  // per-stage event timing
+  static constexpr int kStages = 6;
+  bool timing = false;
+  double stage_ms[kStages] = {0};
+  int64_t stage_n[kStages] = {0};
+  double stage_flops[kStages] = {0};
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+    double flops;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t get_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Resolve recorded event pairs (the stream must have been synchronised).
+  void resolve_timing() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        stage_ms[p.stage] += ms;
+        stage_n[p.stage] += 1;
+        stage_flops[p.stage] += p.flops;
+      }
+      event_pool.push_back(p.a);
+      event_pool.push_back(p.b);
+    }
+    pending.clear();
+  }
 
   void* buf(const char* name) {
     for (auto& b : bufs)
@@ -105,10 +142,35 @@ struct isdf_handle {
 
 namespace {
 
+// Records a CUDA event pair around a block of launches of one stage.
+struct StageTimer {
+  isdf_handle* h;
+  int stage;
+  double flops;
+  cudaEvent_t a = nullptr;
+  StageTimer(isdf_handle* hh, int st, double fl) : h(hh), stage(st), flops(fl) {
+    if (h->timing) {
+      a = h->get_event();
+      cudaEventRecord(a, h->st);
+    }
+  }
+  ~StageTimer() {
+    if (h->timing && a) {
+      cudaEvent_t b = h->get_event();
+      cudaEventRecord(b, h->st);
+      h->pending.push_back({stage, a, b, flops});
+    }
+  }
+};
+
 struct LaunchScope {
   int64_t* prev;
-  explicit LaunchScope(isdf_handle* h) : prev(g_launch_counter) { g_launch_counter = &h->launches; }
-  ~LaunchScope() { g_launch_counter = prev; }
+  isdf_handle* h;
+  explicit LaunchScope(isdf_handle* hh) : prev(g_launch_counter), h(hh) { g_launch_counter = &h->launches; }
+  ~LaunchScope() {
+    g_launch_counter = prev;
+    if (!h->pending.empty() && cudaStreamSynchronize(h->st) == cudaSuccess) h->resolve_timing();
+  }
 };
 
 int fail(isdf_handle* h, int code, const char* fmt, ...) {
@@ -148,6 +210,14 @@ double prim_norm(double a, int lx, int ly, int lz) {
   const double n2 = std::pow(2.0 * a / M_PI, 1.5) * std::pow(4.0 * a, l) /
                     (dfact(2 * lx - 1) * dfact(2 * ly - 1) * dfact(2 * lz - 1));
   return std::sqrt(n2);
+}
+
+// Algorithmic flops of the pair tensor: T = X C, the k->R DFT of T, the pair
+// products and the R->q DFT (direct per-axis DFTs: n_a complex MACs per point and axis).
+double frag_m_flops(int nk, int np, int nf, int nao, const KMesh& km) {
+  const double per_pt = 8.0 * (km.n[0] + km.n[1] + km.n[2]);
+  return 8.0 * nk * (double)np * nf * nao + per_pt * nk * (double)np * nf + 6.0 * nk * (double)nf * nf * np +
+         per_pt * nk * (double)nf * nf * np;
 }
 
 int check_device(isdf_handle* h) {
@@ -332,6 +402,7 @@ int isdf_build_points(isdf_handle* h, int n_p, uint64_t seed, double chol_tol, i
   if (int e = check_device(h)) return e;
   if (n_p < 1 || n_p > h->ng) return fail(h, ISDF_ERR_ARG, "n_p=%d outside [1, N_g=%d]", n_p, h->ng);
   if (!(chol_tol >= 0.0)) return fail(h, ISDF_ERR_ARG, "chol_tol must be >= 0");
+  StageTimer stt(h, 0, 0.0);
   if (int e = eval_phi(h)) return e;
   const int ng = h->ng, nkao = h->nk * h->nao;
   double2* phi = (double2*)h->buf("phi");
@@ -397,6 +468,8 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
   const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
   double2* X = (double2*)h->buf("X");
   double2* phi = (double2*)h->buf("phi");
+  // algorithmic work: g^k GEMM + eta k-convolutions + xi = W eta (complex flops x 8)
+  StageTimer stt(h, 1, 8.0 * nk * (double)np * ng * (nao + np));
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   // Pi^q (Eq. 4): G^k_IJ = sum_mu conj(X^k_I mu) X^k_J mu, then the k-convolution
   ENSURE(Pi, double2, "Pi", (size_t)nk * np * np);
@@ -443,20 +516,14 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
   double2* xi = (double2*)h->buf("xi");
   double2* W = (double2*)h->buf("W");
   const double2* tw = (const double2*)h->buf("grid_tw");
+  StageTimer stt(h, 2, 4.0 * nk * (double)np * np * ng);  // Hermitian V_xi GEMM
   ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
-  if (h->prec == ISDF_FP64) {
-    CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw));
-    CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi, ng, (int64_t)np * ng, xi, ng,
-             (int64_t)np * ng, zero, Vxi, np, (int64_t)np * np, nk));
-  } else {
-    ENSURE(xif, float2, "xi_f", (size_t)nk * np * ng);
-    ENSURE(Vxif, float2, "Vxi_f", (size_t)nk * np * np);
-    CK(z2c(h->st, xi, xif, (int64_t)nk * np * ng));
-    CK(grid_coulomb_fft_f(h->st, xif, np, 0, nk, h->cell, tw));
-    CK(cgemm(h->st, 'R', 'T', np, np, ng, make_float2((float)h->volume, 0.f), xif, ng, (int64_t)np * ng, xif,
-             ng, (int64_t)np * ng, make_float2(0.f, 0.f), Vxif, np, (int64_t)np * np, nk));
-    CK(c2z(h->st, Vxif, Vxi, (int64_t)nk * np * np));
-  }
+  // The Coulomb metric is computed in FP64 in both precisions: V^q carries the
+  // conditioning of the fit (its scale exceeds that of the ERIs by the
+  // cancellation in M V M^H), so its rounding is kept at the FP64 level.
+  CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw));
+  CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi, ng, (int64_t)np * ng, xi, ng,
+           (int64_t)np * ng, zero, Vxi, np, (int64_t)np * np, nk));
   h->has_xi = false;  // xi was transformed in place (FP64) / is no longer needed
   // V_xi = L_xi L_xi^H ; L^q = W^T L_xi
   ENSURE(LtV, double2, "LtV", (size_t)nk * np * np);
@@ -518,18 +585,27 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       double2* X = (double2*)h->buf("X");
       double2* Lq = (double2*)h->buf("Lq");
       ENSURE(T, double2, "frag_T", (size_t)nk * np * nf);
-      CK(zgemm(h->st, 'N', 'N', np, nf, nao, one, X, nao, (int64_t)np * nao, Cf, nf, (int64_t)nao * nf, zero, T,
-               nf, (int64_t)np * nf, nk));
-      CK(kdft_cols(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.0));
       ENSURE(M, double2, "frag_M", (size_t)nk * n2 * np);
-      CK(pair_products(h->st, T, nk, np, nf, M));
-      CK(kdft_cols(h->st, M, n2 * np, km, +1, +1, 0, 1.0 / nk));
       ENSURE(B, double2, "frag_B", (size_t)n2 * nk * np);
-      CK(zgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lq, np, (int64_t)np * np, zero, B,
-               (int64_t)nk * np, np, nk));
       ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
-      CK(zgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0, zero,
-               E, n2, 0, 1));
+      {
+        StageTimer stt(h, 3, frag_m_flops(nk, np, nf, nao, km));
+        CK(zgemm(h->st, 'N', 'N', np, nf, nao, one, X, nao, (int64_t)np * nao, Cf, nf, (int64_t)nao * nf, zero, T,
+                 nf, (int64_t)np * nf, nk));
+        CK(kdft_cols(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.0));
+        CK(pair_products(h->st, T, nk, np, nf, M));
+        CK(kdft_cols(h->st, M, n2 * np, km, +1, +1, 0, 1.0 / nk));
+      }
+      {
+        StageTimer stt(h, 4, 8.0 * (double)n2 * np * np * nk);
+        CK(zgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lq, np, (int64_t)np * np, zero, B,
+                 (int64_t)nk * np, np, nk));
+      }
+      {
+        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nk * np);
+        CK(zgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0,
+                 zero, E, n2, 0, 1));
+      }
       if (eri_out && eri_out[f]) CK(eri_permute(h->st, E, nf, 1.0 / nk, (double2*)eri_out[f]));
       if (want_tr) CK(eri_traces(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf));
     } else {
@@ -537,20 +613,29 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       float2* Xf = (float2*)h->buf("X_f");
       float2* Lqf = (float2*)h->buf("Lq_f");
       ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nf);
-      CK(z2c(h->st, Cf, Cff, (int64_t)nk * nao * nf));
       ENSURE(T, float2, "frag_Tf", (size_t)nk * np * nf);
-      CK(cgemm(h->st, 'N', 'N', np, nf, nao, one, Xf, nao, (int64_t)np * nao, Cff, nf, (int64_t)nao * nf, zero, T,
-               nf, (int64_t)np * nf, nk));
-      CK(kdft_cols_f(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.f));
       ENSURE(M, float2, "frag_Mf", (size_t)nk * n2 * np);
-      CK(pair_products_f(h->st, T, nk, np, nf, M));
-      CK(kdft_cols_f(h->st, M, n2 * np, km, +1, +1, 0, 1.f / nk));
       ENSURE(B, float2, "frag_Bf", (size_t)n2 * nk * np);
-      CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lqf, np, (int64_t)np * np, zero, B,
-               (int64_t)nk * np, np, nk));
       ENSURE(E, float2, "frag_Ef", (size_t)n2 * n2);
-      CK(cgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0, zero,
-               E, n2, 0, 1));
+      {
+        StageTimer stt(h, 3, frag_m_flops(nk, np, nf, nao, km));
+        CK(z2c(h->st, Cf, Cff, (int64_t)nk * nao * nf));
+        CK(cgemm(h->st, 'N', 'N', np, nf, nao, one, Xf, nao, (int64_t)np * nao, Cff, nf, (int64_t)nao * nf, zero, T,
+                 nf, (int64_t)np * nf, nk));
+        CK(kdft_cols_f(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.f));
+        CK(pair_products_f(h->st, T, nk, np, nf, M));
+        CK(kdft_cols_f(h->st, M, n2 * np, km, +1, +1, 0, 1.f / nk));
+      }
+      {
+        StageTimer stt(h, 4, 8.0 * (double)n2 * np * np * nk);
+        CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lqf, np, (int64_t)np * np, zero, B,
+                 (int64_t)nk * np, np, nk));
+      }
+      {
+        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nk * np);
+        CK(cgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0,
+                 zero, E, n2, 0, 1));
+      }
       if (eri_out && eri_out[f]) CK(eri_permute_f(h->st, E, nf, 1.f / nk, (float2*)eri_out[f]));
       if (want_tr) CK(eri_traces_f(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf));
     }
@@ -612,10 +697,40 @@ int isdf_sizes(const isdf_handle* h, int64_t* out) {
 
 int64_t isdf_launch_count(const isdf_handle* h) { return h ? h->launches : 0; }
 
+int isdf_timing_enable(isdf_handle* h, int enable) {
+  if (!h) return ISDF_ERR_ARG;
+  if (!h->pending.empty()) {
+    cudaStreamSynchronize(h->st);
+    h->resolve_timing();
+  }
+  h->timing = enable != 0;
+  if (h->timing)
+    for (int i = 0; i < isdf_handle::kStages; ++i) {
+      h->stage_ms[i] = 0;
+      h->stage_n[i] = 0;
+      h->stage_flops[i] = 0;
+    }
+  return ISDF_OK;
+}
+
+int isdf_timing_get(const isdf_handle* h, int stage, double* ms_total, int64_t* launches, double* flops_total) {
+  if (!h || stage < 0 || stage >= isdf_handle::kStages) return ISDF_ERR_ARG;
+  if (ms_total) *ms_total = h->stage_ms[stage];
+  if (launches) *launches = h->stage_n[stage];
+  if (flops_total) *flops_total = h->stage_flops[stage];
+  return ISDF_OK;
+}
+
 const char* isdf_last_error(const isdf_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
 void isdf_destroy(isdf_handle* h) {
   if (!h) return;
+  if (!h->pending.empty()) cudaStreamSynchronize(h->st);
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->event_pool) cudaEventDestroy(e);
   for (auto& b : h->bufs)
     if (b.second.p) cudaFree(b.second.p);
   delete h;

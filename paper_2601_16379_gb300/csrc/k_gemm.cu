@@ -8,6 +8,10 @@
 // Tiling: 64 x 64 output tile per 256-thread block, each thread owns a 4 x 4
 // sub-tile spread with stride 16 (conflict-free shared reads), K staged 8 (FP64)
 // or 16 (FP32) at a time through shared memory.
+//
+// FP32 accumulation is compensated: each K tile is summed in FP32, then folded
+// into a float-float running sum with TwoSum (Knuth), so the rounding error is
+// that of a 16-term FP32 sum plus ~2^-48 of the total instead of growing with K.
 #include "common.cuh"
 
 namespace isdf {
@@ -38,6 +42,31 @@ __device__ __forceinline__ T conj_if(T v, bool c) {
 __device__ __forceinline__ void cfma_t(double2& acc, double2 a, double2 b) { cfma(acc, a, b); }
 __device__ __forceinline__ void cfma_t(float2& acc, float2 a, float2 b) { cfma(acc, a, b); }
 
+// hi + lo += x, error-free (TwoSum).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float ap = s - bp;
+  lo += (hi - ap) + (x - bp);
+  hi = s;
+}
+__device__ __forceinline__ void fold(double2& acc, double2& lo, double2 part) {
+  acc.x += part.x;
+  acc.y += part.y;
+}
+__device__ __forceinline__ void fold(float2& acc, float2& lo, float2 part) {
+  two_sum_acc(acc.x, lo.x, part.x);
+  two_sum_acc(acc.y, lo.y, part.y);
+}
+template <typename T>
+__device__ __forceinline__ T finish(T acc, T lo);
+template <>
+__device__ __forceinline__ double2 finish(double2 acc, double2) { return acc; }
+template <>
+__device__ __forceinline__ float2 finish(float2 acc, float2 lo) {
+  return make_float2(acc.x + lo.x, acc.y + lo.y);
+}
+
 template <typename T, int BK>
 __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, int n, int k, T alpha,
                                                    const T* __restrict__ A, int64_t lda, int64_t sA,
@@ -59,11 +88,15 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
   const bool bT = (opB == 'T' || opB == 'C');
   const bool bC = (opB == 'C' || opB == 'R');
 
-  T acc[4][4];
+  constexpr bool kComp = sizeof(T) == 8;  // compensated accumulation for FP32
+  T acc[4][4], lo[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = zero_c<T>();
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j] = zero_c<T>();
+      lo[i][j] = zero_c<T>();
+    }
 
   for (int k0 = 0; k0 < k; k0 += BK) {
     // load op(A) tile: BM x BK
@@ -97,17 +130,41 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
       Bs[kk][nn] = conj_if(v, bC);
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      T a[4], bb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+    if constexpr (kComp) {
+      T part[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cfma_t(acc[i][j], a[i], bb[j]);
+        for (int j = 0; j < 4; ++j) part[i][j] = zero_c<T>();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma_t(part[i][j], a[i], bb[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) fold(acc[i][j], lo[i][j], part[i][j]);
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma_t(acc[i][j], a[i], bb[j]);
+      }
     }
     __syncthreads();
   }
@@ -120,7 +177,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= n) continue;
-      T r = cmul(alpha, acc[i][j]);
+      T r = cmul(alpha, finish(acc[i][j], lo[i][j]));
       T* cp = C + (int64_t)gm * ldc + gn;
       if (use_beta) {
         T o = *cp;
