@@ -197,3 +197,4 @@ class Isdf:
     def get(self, what: int, out):
         self._check(self.lib.isdf_get(self.h, int(what), _ptr(out)))
         return out
+

@@ -6,6 +6,7 @@
 
 #include <cstdio>
 #include <string>
+#include <vector>
 
 namespace isdf {
 
@@ -56,6 +57,11 @@ inline void count_launch() {
 cudaError_t zgemm(cudaStream_t st, char opA, char opB, int m, int n, int k, double2 alpha,
                   const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb,
                   int64_t sB, double2 beta, double2* C, int64_t ldc, int64_t sC, int batch);
+// C_b = A_b * gather_rows(B_b, brow_b) with A_b (m x m) lower triangular: the
+// k > row blocks are skipped.  Rows with brow < 0 contribute zero.
+cudaError_t ztrmm_gather(cudaStream_t st, int m, int n, const double2* A, int64_t lda, int64_t sA,
+                         const int32_t* brow, int64_t sIdx, const double2* B, int64_t ldb, int64_t sB, double2* C,
+                         int64_t ldc, int64_t sC, int batch);
 cudaError_t cgemm(cudaStream_t st, char opA, char opB, int m, int n, int k, float2 alpha,
                   const float2* A, int64_t lda, int64_t sA, const float2* B, int64_t ldb,
                   int64_t sB, float2 beta, float2* C, int64_t ldc, int64_t sC, int batch);
@@ -138,6 +144,16 @@ cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale,
                        const double2* gamma, double* out2);
 cudaError_t eri_traces_f(cudaStream_t st, const float2* E, int nf, double scale,
                          const double2* gamma, double* out2);
+
+// Tensor-core E = scale * B B^H (k_tc.cu); B complex64 n2 x K with row pitch ldb,
+// E complex128 n2 x n2 (full Hermitian).  Workspace sizes from the helpers below.
+size_t herk_tc_split_bytes(int64_t n2, int64_t K);
+void herk_tc_tiles(int64_t n2, std::vector<int2>& tiles);
+size_t herk_tc_ws_bytes(int64_t ntiles);
+cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int64_t ldb, double scale,
+                    void* split, const int2* tiles_d, int ntiles, void* ws, int* err, double2* E);
+// eri[p][q][r][s] (complex64) = E[(p q)][(s r)] (complex128) * scale
+cudaError_t eri_permute_zc(cudaStream_t st, const double2* E, int nf, double scale, float2* eri);
 
 // Precision conversions.
 cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n);

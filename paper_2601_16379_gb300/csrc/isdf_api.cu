@@ -62,6 +62,7 @@ struct isdf_handle {
   std::vector<int32_t> ranks;
   std::string err;
   int64_t launches = 0;
+  std::vector<int2> tiles_host;
   // per-stage event timing
   static constexpr int kStages = 6;
   bool timing = false;
@@ -490,10 +491,10 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
   ENSURE(W, double2, "W", (size_t)nk * np * np);
   ENSURE(wwork, double2, "W_work", (size_t)nk * np * np);
   CK(trinv_batched(h->st, LtPi, permPi, rankPi, np, nk, W, wwork));
-  // xi^q = W eta^q
+  // xi^q = W eta^q = L_S^{-1} (eta^q rows in pivot order): triangular, gathered
   ENSURE(xi, double2, "xi", (size_t)nk * np * ng);
-  CK(zgemm(h->st, 'N', 'N', np, ng, np, one, W, np, (int64_t)np * np, eta, ng, (int64_t)np * ng, zero, xi, ng,
-           (int64_t)np * ng, nk));
+  CK(ztrmm_gather(h->st, np, ng, wwork, np, (int64_t)np * np, permPi, np, eta, ng, (int64_t)np * ng, xi, ng,
+                  (int64_t)np * ng, nk));
   h->ranks.assign(nk, 0);
   CK(cudaMemcpyAsync(h->ranks.data(), rankPi, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -616,7 +617,17 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       ENSURE(T, float2, "frag_Tf", (size_t)nk * np * nf);
       ENSURE(M, float2, "frag_Mf", (size_t)nk * n2 * np);
       ENSURE(B, float2, "frag_Bf", (size_t)n2 * nk * np);
-      ENSURE(E, float2, "frag_Ef", (size_t)n2 * n2);
+      ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
+      std::vector<int2>& tl = h->tiles_host;
+      herk_tc_tiles(n2, tl);
+      const int64_t Kq = (int64_t)nk * np;
+      ENSURE(split, uint8_t, "tc_split", herk_tc_split_bytes(n2, Kq));
+      ENSURE(tiles_d, int2, "tc_tiles", tl.size());
+      ENSURE(ws, uint8_t, "tc_ws", herk_tc_ws_bytes((int64_t)tl.size()));
+      ENSURE(tcw, int, "tc_words", 4);
+      CK(cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
+      CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
+
       {
         StageTimer stt(h, 3, frag_m_flops(nk, np, nf, nao, km));
         CK(z2c(h->st, Cf, Cff, (int64_t)nk * nao * nf));
@@ -633,11 +644,15 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       }
       {
         StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nk * np);
-        CK(cgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0,
-                 zero, E, n2, 0, 1));
+        CK(herk_tc(h->st, B, n2, Kq, Kq, 1.0 / nk, split, tiles_d, (int)tl.size(), ws, tcw + 1, E));
       }
-      if (eri_out && eri_out[f]) CK(eri_permute_f(h->st, E, nf, 1.f / nk, (float2*)eri_out[f]));
-      if (want_tr) CK(eri_traces_f(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf));
+      if (eri_out && eri_out[f]) CK(eri_permute_zc(h->st, E, nf, 1.0, (float2*)eri_out[f]));
+      if (want_tr) CK(eri_traces(h->st, E, nf, 1.0, (const double2*)gamma[f], trf));
+      int tc_err = 0;
+      CK(cudaMemcpyAsync(&tc_err, tcw + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      if (tc_err != 0)
+        return fail(h, ISDF_ERR_TIMEOUT, "tensor-core contraction: bounded device wait expired (code %d)", tc_err);
     }
     if (want_tr) {
       double hv[4];

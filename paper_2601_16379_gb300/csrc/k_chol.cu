@@ -184,9 +184,13 @@ cudaError_t trinv_batched(cudaStream_t st, const double2* Lt, const int32_t* per
                           int n, int batch, double2* W, double2* work) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
   dim3 g((n + 255) / 256, batch);
+  // work holds L_S^{-1} in pivot order (lower triangular); entries outside the
+  // rank stay zero
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double2) * (size_t)batch * n * n, st);
+  if (e != cudaSuccess) return e;
   trinv_kernel<<<g, 256, 0, st>>>(Lt, perm, rank, n, work);
   count_launch();
-  cudaError_t e = cudaMemsetAsync(W, 0, sizeof(double2) * (size_t)batch * n * n, st);
+  e = cudaMemsetAsync(W, 0, sizeof(double2) * (size_t)batch * n * n, st);
   if (e != cudaSuccess) return e;
   scatter_w_kernel<<<nblocks((int64_t)batch * n * n), 256, 0, st>>>(work, perm, rank, n, batch, W);
   count_launch();

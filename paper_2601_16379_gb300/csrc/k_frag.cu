@@ -13,8 +13,8 @@ namespace isdf {
 
 namespace {
 
-template <typename T>
-__global__ void eri_permute_kernel(const T* __restrict__ E, int nf, double scale, T* __restrict__ eri) {
+template <typename T, typename TO = T>
+__global__ void eri_permute_kernel(const T* __restrict__ E, int nf, double scale, TO* __restrict__ eri) {
   const int64_t n2 = (int64_t)nf * nf;
   const int64_t total = n2 * n2;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -22,10 +22,11 @@ __global__ void eri_permute_kernel(const T* __restrict__ E, int nf, double scale
     const int s = (int)(e % nf);
     const int r = (int)((e / nf) % nf);
     const int64_t pq = e / n2;
-    T v = E[pq * n2 + (int64_t)s * nf + r];
-    v.x *= scale;
-    v.y *= scale;
-    eri[e] = v;
+    const T v = E[pq * n2 + (int64_t)s * nf + r];
+    TO o;
+    o.x = v.x * scale;
+    o.y = v.y * scale;
+    eri[e] = o;
   }
 }
 
@@ -117,6 +118,11 @@ inline int nblocks(int64_t total) {
 
 cudaError_t eri_permute(cudaStream_t st, const double2* E, int nf, double scale, double2* eri) {
   eri_permute_kernel<double2><<<nblocks((int64_t)nf * nf * nf * nf), 256, 0, st>>>(E, nf, scale, eri);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t eri_permute_zc(cudaStream_t st, const double2* E, int nf, double scale, float2* eri) {
+  eri_permute_kernel<double2, float2><<<nblocks((int64_t)nf * nf * nf * nf), 256, 0, st>>>(E, nf, scale, eri);
   count_launch();
   return cudaGetLastError();
 }

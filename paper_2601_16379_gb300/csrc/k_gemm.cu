@@ -67,12 +67,16 @@ __device__ __forceinline__ float2 finish(float2 acc, float2 lo) {
   return make_float2(acc.x + lo.x, acc.y + lo.y);
 }
 
+// Optional structure: lowerA skips the k > row part of a lower-triangular
+// op(A); brow (with batch stride sIdx) gathers the rows of B ('N' only):
+// op(B)[kk][n] = B[brow[kk]][n], 0 where brow[kk] < 0.
 template <typename T, int BK>
 __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, int n, int k, T alpha,
                                                    const T* __restrict__ A, int64_t lda, int64_t sA,
                                                    const T* __restrict__ B, int64_t ldb, int64_t sB,
                                                    T beta, T* __restrict__ C, int64_t ldc,
-                                                   int64_t sC) {
+                                                   int64_t sC, int lowerA, const int32_t* __restrict__ brow,
+                                                   int64_t sIdx) {
   constexpr int BM = 64, BN = 64;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
@@ -83,6 +87,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
   A += b * sA;
   B += b * sB;
   C += b * sC;
+  if (brow) brow += b * sIdx;
+  const int kend = lowerA ? min(k, m0 + BM) : k;
   const bool aT = (opA == 'T' || opA == 'C');
   const bool aC = (opA == 'C' || opA == 'R');
   const bool bT = (opB == 'T' || opB == 'C');
@@ -98,7 +104,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
       lo[i][j] = zero_c<T>();
     }
 
-  for (int k0 = 0; k0 < k; k0 += BK) {
+  for (int k0 = 0; k0 < kend; k0 += BK) {
     // load op(A) tile: BM x BK
     for (int e = tid; e < BM * BK; e += 256) {
       int mm, kk;
@@ -126,7 +132,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
       }
       const int gn = n0 + nn, gk = k0 + kk;
       T v = zero_c<T>();
-      if (gn < n && gk < k) v = bT ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+      if (gn < n && gk < k) {
+        if (brow) {
+          const int rr = brow[gk];
+          if (rr >= 0) v = B[(int64_t)rr * ldb + gn];
+        } else {
+          v = bT ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+        }
+      }
       Bs[kk][nn] = conj_if(v, bC);
     }
     __syncthreads();
@@ -193,22 +206,25 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
 template <typename T, int BK>
 static cudaError_t gemm_launch(cudaStream_t st, char opA, char opB, int m, int n, int k, T alpha,
                                const T* A, int64_t lda, int64_t sA, const T* B, int64_t ldb,
-                               int64_t sB, T beta, T* C, int64_t ldc, int64_t sC, int batch) {
+                               int64_t sB, T beta, T* C, int64_t ldc, int64_t sC, int batch,
+                               int lowerA = 0, const int32_t* brow = nullptr, int64_t sIdx = 0) {
   if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535) {
     // split very large batches
     for (int b0 = 0; b0 < batch; b0 += 65535) {
       int nb = batch - b0 < 65535 ? batch - b0 : 65535;
       cudaError_t e = gemm_launch<T, BK>(st, opA, opB, m, n, k, alpha, A + b0 * sA, lda, sA,
-                                         B + b0 * sB, ldb, sB, beta, C + b0 * sC, ldc, sC, nb);
+                                         B + b0 * sB, ldb, sB, beta, C + b0 * sC, ldc, sC, nb, lowerA,
+                                         brow ? brow + b0 * sIdx : nullptr, sIdx);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
   dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
   if (grid.y > 65535) return cudaErrorInvalidValue;
+  if (brow && opB != 'N') return cudaErrorInvalidValue;
   gemm_kernel<T, BK><<<grid, 256, 0, st>>>(opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta,
-                                           C, ldc, sC);
+                                           C, ldc, sC, lowerA, brow, sIdx);
   count_launch();
   return cudaGetLastError();
 }
@@ -218,6 +234,13 @@ cudaError_t zgemm(cudaStream_t st, char opA, char opB, int m, int n, int k, doub
                   int64_t sB, double2 beta, double2* C, int64_t ldc, int64_t sC, int batch) {
   return gemm_launch<double2, 8>(st, opA, opB, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C,
                                  ldc, sC, batch);
+}
+
+cudaError_t ztrmm_gather(cudaStream_t st, int m, int n, const double2* A, int64_t lda, int64_t sA,
+                         const int32_t* brow, int64_t sIdx, const double2* B, int64_t ldb, int64_t sB, double2* C,
+                         int64_t ldc, int64_t sC, int batch) {
+  return gemm_launch<double2, 8>(st, 'N', 'N', m, n, m, make_double2(1.0, 0.0), A, lda, sA, B, ldb, sB,
+                                 make_double2(0.0, 0.0), C, ldc, sC, batch, 1, brow, sIdx);
 }
 
 cudaError_t cgemm(cudaStream_t st, char opA, char opB, int m, int n, int k, float2 alpha,

@@ -8,16 +8,22 @@
 // B' = the P rows (every other row of A') yields both parts.  Only tiles that
 // touch the lower triangle of the Hermitian E are computed.
 //
-// Precision: every real value is split as x = hi + lo with hi = fp16(s x) and
-// lo = fp16(s x - hi) (s a power of two), and D = Ah Bh^T + Ah Bl^T + Al Bh^T
-// is accumulated by tcgen05.mma kind::f16 in FP32 TMEM.  The accumulator is
-// flushed every `flush` k-blocks into an FP64 workspace (double-buffered TMEM,
-// the flush overlaps the next chunk's MMAs), so FP32 accumulation only spans
-// short chunks.
+// Precision (error-free slicing after Ozaki, Ogita, Oishi & Rump, 2012): each
+// complex row a is scaled by a power of two 2^e_a so that its largest real
+// component lies in [64, 128), and every scaled value is written as
+//     v = s1 + s2/128 + s3/128^2 (+ remainder below 2^-15),  s_i integers, |s1| <= 128, |s2|, |s3| <= 64,
+// stored as fp16 (exact).  The tcgen05.mma kind::f16 products of integer
+// slices are integers, and the three weight groups
+//     g0 = S1.T1,  g1 = S1.T2 + S2.T1,  g2 = S1.T3 + S2.T2 + S3.T1
+// are accumulated in three FP32 TMEM accumulators.  A chunk of at most 48
+// k-steps keeps every partial sum an integer below 2^24, so the FP32
+// accumulation is exact whatever its rounding; after each chunk the epilogue
+// adds (g0, g1/128 + g2/128^2) into a float-float (TwoSum) accumulator in
+// global memory.  The result is accurate to ~2^-22 of |B_a||B_b| and unbiased.
 //
 // Kernel roles (192 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
-// and issues the MMAs, warps 2-5 drain TMEM into the FP64 workspace.  Every
-// wait is bounded: on expiry the CTA records an error code and exits.
+// and issues the MMAs, warps 2-5 drain TMEM into the float-float workspace.
+// Every wait is bounded: on expiry the CTA records an error code and exits.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -31,14 +37,16 @@ namespace isdf {
 namespace tc {
 
 constexpr int BM = 128;        // A' rows per tile (64 complex rows of E)
-constexpr int BN = 256;        // B' rows per tile (complex columns of E)
+constexpr int BN = 128;        // B' rows per tile (complex columns of E)
 constexpr int BK = 64;         // fp16 per row per stage (one 128-byte swizzle row)
 constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;        // 16 KB
-constexpr int B_BYTES = BN * BK * 2;        // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // Ah, Al, Bh, Bl: 96 KB
-constexpr int TMEM_COLS = 512;              // two 256-column FP32 accumulators
+constexpr int NSLICE = 3;
+constexpr int A_BYTES = BM * BK * 2;        // 16 KB per slice
+constexpr int B_BYTES = BN * BK * 2;        // 16 KB per slice
+constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);  // 96 KB
+constexpr int TMEM_COLS = 512;              // three 128-column FP32 accumulators (power-of-two allocation)
 constexpr int NTHREADS = 192;
+constexpr int kChunkKB = 12;                // k-blocks per exact chunk: 48 k-steps of 16
 constexpr unsigned long long kWaitNs = 4000000000ULL;  // bounded waits: 4 s of device time
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -63,13 +71,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of parity `parity`; false on timeout or if another
-// thread of the CTA already gave up.
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// Bounded wait for the phase of parity `parity`; false on timeout or if another
+// thread of the CTA already gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* s_err, int* g_err,
                                           int code) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -131,40 +139,39 @@ constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t
 
 struct TileArgs {
   const int2* tiles;   // (ti, tj) per CTA
-  double* ws;          // [tile][BN][BM] FP64 partial sums
+  float* ws_hi;        // [tile][BN][BM] float-float sums, high part
+  float* ws_lo;        // low part
   int nkb;             // k-blocks of BK
-  int flush;           // k-blocks per TMEM chunk
   int* err;            // device error word
 };
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    herk_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-                   const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TileArgs args) {
+    herk_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
+                   const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mB1,
+                   const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, TileArgs args) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment of the shared-window address (128-byte swizzle atoms)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* full = bars;                 // [STAGES]
-  uint64_t* empty = bars + STAGES;       // [STAGES]
-  uint64_t* accf = bars + 2 * STAGES;    // [2]
-  uint64_t* acce = bars + 2 * STAGES + 2;  // [2]
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  uint64_t* full = bars;                   // [STAGES]
+  uint64_t* empty = bars + STAGES;         // [STAGES]
+  uint64_t* accf = bars + 2 * STAGES;      // chunk accumulated
+  uint64_t* acce = bars + 2 * STAGES + 1;  // chunk drained
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
   volatile int* s_err = reinterpret_cast<volatile int*>(s_tmem + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int2 tile = args.tiles[blockIdx.x];
-  const int nkb = args.nkb, F = args.flush;
-  const int nchunks = (nkb + F - 1) / F;
+  const int nkb = args.nkb;
+  const int nchunks = (nkb + kChunkKB - 1) / kChunkKB;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 128);
-    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 128);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -181,70 +188,94 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
+      const CUtensorMap* ma[3] = {&mA1, &mA2, &mA3};
+      const CUtensorMap* mb[3] = {&mB1, &mB2, &mB3};
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
         if (!mbar_wait(&empty[s], (r & 1) ^ 1, s_err, args.err, 1)) break;
         uint8_t* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
         const int x = kb * BK;
-        tma_load_2d(st, &mAh, &full[s], x, tile.x * BM);
-        tma_load_2d(st + A_BYTES, &mAl, &full[s], x, tile.x * BM);
-        tma_load_2d(st + 2 * A_BYTES, &mBh, &full[s], x, tile.y * BN);
-        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBl, &full[s], x, tile.y * BN);
+#pragma unroll
+        for (int i = 0; i < NSLICE; ++i) {
+          tma_load_2d(st + i * A_BYTES, ma[i], &full[s], x, tile.x * BM);
+          tma_load_2d(st + NSLICE * A_BYTES + i * B_BYTES, mb[i], &full[s], x, tile.y * BN);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
-        const int c = kb / F, buf = c & 1, u = c >> 1;
-        const bool first_in_chunk = (kb % F) == 0;
-        if (first_in_chunk) {
-          if (!mbar_wait(&acce[buf], (u & 1) ^ 1, s_err, args.err, 2)) break;
+        const int c = kb / kChunkKB;
+        const bool first_in_chunk = (kb % kChunkKB) == 0;
+        if (first_in_chunk && c > 0) {
+          // the epilogue must have drained the previous chunk
+          if (!mbar_wait(acce, (c - 1) & 1, s_err, args.err, 2)) break;
           tc_fence_after();
         }
         if (!mbar_wait(&full[s], r & 1, s_err, args.err, 3)) break;
         tc_fence_after();
         const uint8_t* st = smem + s * STAGE_BYTES;
-        const uint64_t dAh = sdesc_sw128(st), dAl = sdesc_sw128(st + A_BYTES);
-        const uint64_t dBh = sdesc_sw128(st + 2 * A_BYTES), dBl = sdesc_sw128(st + 2 * A_BYTES + B_BYTES);
-        const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+        uint64_t dA[3], dB[3];
+#pragma unroll
+        for (int i = 0; i < NSLICE; ++i) {
+          dA[i] = sdesc_sw128(st + i * A_BYTES);
+          dB[i] = sdesc_sw128(st + NSLICE * A_BYTES + i * B_BYTES);
+        }
+        const uint32_t g0 = tmem_base, g1 = tmem_base + BN, g2 = tmem_base + 2 * BN;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 fp16 = 32 bytes along K
-          umma_f16(d, dAh + off, dBh + off, kIdesc, (first_in_chunk && kk == 0) ? 0u : 1u);
-          umma_f16(d, dAh + off, dBl + off, kIdesc, 1u);
-          umma_f16(d, dAl + off, dBh + off, kIdesc, 1u);
+          const uint32_t acc = (first_in_chunk && kk == 0) ? 0u : 1u;
+          umma_f16(g0, dA[0] + off, dB[0] + off, kIdesc, acc);
+          umma_f16(g1, dA[0] + off, dB[1] + off, kIdesc, acc);
+          umma_f16(g1, dA[1] + off, dB[0] + off, kIdesc, 1u);
+          umma_f16(g2, dA[0] + off, dB[2] + off, kIdesc, acc);
+          umma_f16(g2, dA[1] + off, dB[1] + off, kIdesc, 1u);
+          umma_f16(g2, dA[2] + off, dB[0] + off, kIdesc, 1u);
         }
         umma_commit(&empty[s]);
-        if ((kb % F) == F - 1 || kb == nkb - 1) umma_commit(&accf[buf]);
+        if ((kb % kChunkKB) == kChunkKB - 1 || kb == nkb - 1) umma_commit(accf);
       }
     }
   } else {
     // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    double* ws = args.ws + (size_t)blockIdx.x * BN * BM;
+    float* wh = args.ws_hi + (size_t)blockIdx.x * BN * BM;
+    float* wl = args.ws_lo + (size_t)blockIdx.x * BN * BM;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     for (int c = 0; c < nchunks; ++c) {
-      const int buf = c & 1, u = c >> 1;
-      if (!mbar_wait(&accf[buf], u & 1, s_err, args.err, 4)) break;
+      if (!mbar_wait(accf, c & 1, s_err, args.err, 4)) break;
       tc_fence_after();
 #pragma unroll 1
       for (int cb = 0; cb < BN / 32; ++cb) {
-        uint32_t v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + cb * 32), v);
+        uint32_t v0[32], v1[32], v2[32];
+        tmem_ld32(tmem_base + lane_off + (uint32_t)(cb * 32), v0);
+        tmem_ld32(tmem_base + lane_off + (uint32_t)(BN + cb * 32), v1);
+        tmem_ld32(tmem_base + lane_off + (uint32_t)(2 * BN + cb * 32), v2);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          double* p = ws + (size_t)(cb * 32 + j) * BM + row;
-          const double x = (double)__uint_as_float(v[j]);
-          if (c == 0)
-            *p = x;
-          else
-            *p += x;
+          const size_t idx = (size_t)(cb * 32 + j) * BM + row;
+          const float a0 = __uint_as_float(v0[j]);
+          const float t = fmaf(__uint_as_float(v2[j]), 1.0f / 16384.0f, __uint_as_float(v1[j]) * (1.0f / 128.0f));
+          if (c == 0) {
+            wh[idx] = a0;
+            wl[idx] = t;
+          } else {
+            // (H, L) += (a0, t) with TwoSum on the high parts
+            const float H = wh[idx];
+            const float S = H + a0;
+            const float bp = S - H;
+            const float e = (H - (S - bp)) + (a0 - bp);
+            wh[idx] = S;
+            wl[idx] = wl[idx] + (e + t);
+          }
         }
       }
       tc_fence_before();
-      mbar_arrive(&acce[buf]);
+      mbar_arrive(acce);
     }
   }
   tc_fence_before();
@@ -257,55 +288,67 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ----------------------------------------------------------------- helpers
-__global__ void maxabs_kernel(const float2* __restrict__ B, int64_t rows, int64_t cols, int64_t ld,
-                              unsigned int* __restrict__ out_bits) {
+// Per complex row a: exponent e_a with max_k max(|Re B_ak|, |Im B_ak|) 2^e_a in [64, 128).
+__global__ void row_scale_kernel(const float2* __restrict__ B, int64_t n2, int64_t K, int64_t ld,
+                                 int* __restrict__ row_exp) {
+  const int64_t a = blockIdx.x;
+  if (a >= n2) return;
   float m = 0.f;
-  const int64_t total = rows * cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = B[(e / cols) * ld + (e % cols)];
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+    const float2 v = B[a * ld + k];
     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
+  __shared__ float sm[32];
   for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));  // non-negative floats order as uints
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmaxf(mm, sm[i]);
+    row_exp[a] = (mm > 0.f && isfinite(mm)) ? 6 - ilogbf(mm) : 0;
+  }
 }
 
-// A'[2a][2k] = s Re B_ak, A'[2a][2k+1] = s Im B_ak, A'[2a+1][2k] = s Im B_ak, A'[2a+1][2k+1] = -s Re B_ak,
-// split into hi = fp16(x), lo = fp16(x - hi); columns beyond 2K are zero.
+// Slices of A': row 2a = P_a (Re, Im interleaved), row 2a+1 = Q_a (Im, -Re); columns
+// beyond 2K are zero.  v = x 2^e_a = s1 + s2/128 + s3/128^2 (+ remainder).
 __global__ void split_kernel(const float2* __restrict__ B, int64_t n2, int64_t K, int64_t ld, int64_t K2,
-                             const unsigned int* __restrict__ maxbits, __half* __restrict__ Ah,
-                             __half* __restrict__ Al) {
-  const float mx = __uint_as_float(*maxbits);
-  // scale: power of two bringing the largest entry to about 2^12
-  const float s = mx > 0.f ? exp2f(floorf(12.f - log2f(mx))) : 1.f;
+                             const int* __restrict__ row_exp, __half* __restrict__ S1, __half* __restrict__ S2,
+                             __half* __restrict__ S3) {
   const int64_t total = n2 * (K2 / 2);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = e / (K2 / 2), k = e % (K2 / 2);
     float2 v = make_float2(0.f, 0.f);
     if (k < K) v = B[a * ld + k];
-    const float pr = s * v.x, pi = s * v.y;
+    const int ex = row_exp[a];
+    const float pr = ldexpf(v.x, ex), pi = ldexpf(v.y, ex);
     const float vals[4] = {pr, pi, pi, -pr};
-    __half hi[4], lo[4];
+    __half h1[4], h2[4], h3[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      hi[t] = __float2half_rn(vals[t]);
-      lo[t] = __float2half_rn(vals[t] - __half2float(hi[t]));
+      const float s1 = rintf(vals[t]);
+      const float r1 = (vals[t] - s1) * 128.f;
+      const float s2 = rintf(r1);
+      const float r2 = (r1 - s2) * 128.f;
+      const float s3 = rintf(r2);
+      h1[t] = __float2half_rn(s1);
+      h2[t] = __float2half_rn(s2);
+      h3[t] = __float2half_rn(s3);
     }
     const int64_t rP = (2 * a) * K2 + 2 * k, rQ = (2 * a + 1) * K2 + 2 * k;
-    *reinterpret_cast<__half2*>(Ah + rP) = __halves2half2(hi[0], hi[1]);
-    *reinterpret_cast<__half2*>(Al + rP) = __halves2half2(lo[0], lo[1]);
-    *reinterpret_cast<__half2*>(Ah + rQ) = __halves2half2(hi[2], hi[3]);
-    *reinterpret_cast<__half2*>(Al + rQ) = __halves2half2(lo[2], lo[3]);
+    *reinterpret_cast<__half2*>(S1 + rP) = __halves2half2(h1[0], h1[1]);
+    *reinterpret_cast<__half2*>(S2 + rP) = __halves2half2(h2[0], h2[1]);
+    *reinterpret_cast<__half2*>(S3 + rP) = __halves2half2(h3[0], h3[1]);
+    *reinterpret_cast<__half2*>(S1 + rQ) = __halves2half2(h1[2], h1[3]);
+    *reinterpret_cast<__half2*>(S2 + rQ) = __halves2half2(h2[2], h2[3]);
+    *reinterpret_cast<__half2*>(S3 + rQ) = __halves2half2(h3[2], h3[3]);
   }
 }
 
-// E (complex128, n2 x n2, Hermitian) from the FP64 tile workspace, scaled by
-// scale / s^2 where s is the split scale.
-__global__ void herk_finish_kernel(const double* __restrict__ ws, const int2* __restrict__ tiles, int ntiles,
-                                   int64_t n2, const unsigned int* __restrict__ maxbits, double scale,
-                                   double2* __restrict__ E) {
-  const float mx = __uint_as_float(*maxbits);
-  const double s = mx > 0.f ? (double)exp2f(floorf(12.f - log2f(mx))) : 1.0;
-  const double f = scale / (s * s);
+// E (complex128, n2 x n2, Hermitian) from the float-float tile workspace,
+// scaled by scale * 2^-(e_a + e_b).
+__global__ void herk_finish_kernel(const float* __restrict__ wh, const float* __restrict__ wl,
+                                   const int2* __restrict__ tiles, int ntiles, int64_t n2,
+                                   const int* __restrict__ row_exp, double scale, double2* __restrict__ E) {
   const int64_t per = (int64_t)BN * (BM / 2);
   const int64_t total = per * ntiles;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -315,8 +358,10 @@ __global__ void herk_finish_kernel(const double* __restrict__ ws, const int2* __
     const int64_t a = (int64_t)tiles[t].x * (BM / 2) + al;
     const int64_t b = (int64_t)tiles[t].y * BN + c;
     if (a >= n2 || b >= n2 || a < b) continue;
-    const double* w = ws + ((size_t)t * BN + c) * BM;
-    const double re = w[2 * al] * f, im = w[2 * al + 1] * f;
+    const size_t base = ((size_t)t * BN + c) * BM;
+    const double f = ldexp(scale, -(row_exp[a] + row_exp[b]));
+    const double re = ((double)wh[base + 2 * al] + (double)wl[base + 2 * al]) * f;
+    const double im = ((double)wh[base + 2 * al + 1] + (double)wl[base + 2 * al + 1]) * f;
     E[a * n2 + b] = make_double2(re, im);
     if (a != b) E[b * n2 + a] = make_double2(re, -im);
   }
@@ -363,7 +408,7 @@ inline int nblk(int64_t total) {
 
 size_t herk_tc_split_bytes(int64_t n2, int64_t K) {
   const int64_t K2 = ((2 * K + tc::BK - 1) / tc::BK) * tc::BK;
-  return (size_t)2 * (2 * n2) * K2 * sizeof(__half);  // hi and lo
+  return (size_t)tc::NSLICE * (2 * n2) * K2 * sizeof(__half) + (size_t)n2 * sizeof(int) + 256;
 }
 
 void herk_tc_tiles(int64_t n2, std::vector<int2>& tiles) {
@@ -374,38 +419,40 @@ void herk_tc_tiles(int64_t n2, std::vector<int2>& tiles) {
       if (ti * (tc::BM / 2) + (tc::BM / 2 - 1) >= tj * tc::BN) tiles.push_back(make_int2((int)ti, (int)tj));
 }
 
-size_t herk_tc_ws_bytes(int64_t ntiles) { return (size_t)ntiles * tc::BN * tc::BM * sizeof(double); }
+size_t herk_tc_ws_bytes(int64_t ntiles) { return (size_t)ntiles * tc::BN * tc::BM * 2 * sizeof(float); }
 
 // E (complex128 n2 x n2) = scale * B B^H, B complex64 n2 x K (row pitch ldb).
 // split: device buffer of herk_tc_split_bytes; tiles_d: device copy of herk_tc_tiles;
-// ws: herk_tc_ws_bytes; scratch_u32: 1 device word; err: 1 device int (0 on entry).
+// ws: herk_tc_ws_bytes; err: 1 device int (0 on entry).
 cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int64_t ldb, double scale,
-                    void* split, const int2* tiles_d, int ntiles, double* ws, unsigned int* scratch_u32, int* err,
-                    double2* E, int flush) {
+                    void* split, const int2* tiles_d, int ntiles, void* ws, int* err, double2* E) {
   using namespace tc;
   if (n2 <= 0 || K <= 0 || ntiles <= 0) return cudaSuccess;
   const int64_t K2 = ((2 * K + BK - 1) / BK) * BK;
-  __half* Ah = reinterpret_cast<__half*>(split);
-  __half* Al = Ah + (size_t)(2 * n2) * K2;
-  cudaError_t e = cudaMemsetAsync(scratch_u32, 0, sizeof(unsigned int), st);
-  if (e != cudaSuccess) return e;
-  maxabs_kernel<<<nblk(n2 * K), 256, 0, st>>>(B, n2, K, ldb, scratch_u32);
+  __half* S1 = reinterpret_cast<__half*>(split);
+  __half* S2 = S1 + (size_t)(2 * n2) * K2;
+  __half* S3 = S2 + (size_t)(2 * n2) * K2;
+  int* row_exp = reinterpret_cast<int*>(S3 + (size_t)(2 * n2) * K2);
+  row_scale_kernel<<<(unsigned)n2, 256, 0, st>>>(B, n2, K, ldb, row_exp);
   count_launch();
-  split_kernel<<<nblk(n2 * (K2 / 2)), 256, 0, st>>>(B, n2, K, ldb, K2, scratch_u32, Ah, Al);
+  split_kernel<<<nblk(n2 * (K2 / 2)), 256, 0, st>>>(B, n2, K, ldb, K2, row_exp, S1, S2, S3);
   count_launch();
-  CUtensorMap mAh, mAl, mBh, mBl;
-  if (!make_map(&mAh, Ah, K2, 2 * n2, K2, BM) || !make_map(&mAl, Al, K2, 2 * n2, K2, BM) ||
-      !make_map(&mBh, Ah, K2, n2, 2 * K2, BN) || !make_map(&mBl, Al, K2, n2, 2 * K2, BN))
-    return cudaErrorInvalidValue;
+  CUtensorMap mA[3], mB[3];
+  __half* sl[3] = {S1, S2, S3};
+  for (int i = 0; i < 3; ++i)
+    if (!make_map(&mA[i], sl[i], K2, 2 * n2, K2, BM) || !make_map(&mB[i], sl[i], K2, n2, 2 * K2, BN))
+      return cudaErrorInvalidValue;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-  e = cudaFuncSetAttribute(herk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  TileArgs args{tiles_d, ws, (int)(K2 / BK), flush < 1 ? 1 : flush, err};
-  herk_tc_kernel<<<ntiles, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
+  float* wh = reinterpret_cast<float*>(ws);
+  float* wl = wh + (size_t)ntiles * BN * BM;
+  TileArgs args{tiles_d, wh, wl, (int)(K2 / BK), err};
+  herk_tc_kernel<<<ntiles, NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], args);
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  herk_finish_kernel<<<nblk((int64_t)ntiles * BN * (BM / 2)), 256, 0, st>>>(ws, tiles_d, ntiles, n2, scratch_u32,
+  herk_finish_kernel<<<nblk((int64_t)ntiles * BN * (BM / 2)), 256, 0, st>>>(wh, wl, tiles_d, ntiles, n2, row_exp,
                                                                             scale, E);
   count_launch();
   return cudaGetLastError();
