@@ -167,6 +167,30 @@ int isdf_timing_enable(isdf_handle* h, int enable);
 int isdf_timing_get(const isdf_handle* h, int stage, double* ms_total, int64_t* launches,
                     double* flops_total);
 
+/* Allocation-free variant of the fragment trace reduction.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory -- for example a host application whose own allocator owns the GPU's
+ * memory and forbids libraries to call cudaMalloc, or a latency-critical loop
+ * that cannot afford the implicit synchronisation of an allocation.
+ *   eri      device complex128 [p][q][r][s] chemist's (pq|rs) of one fragment
+ *            (as written by isdf_fragment_eri in FP64 mode)
+ *   gamma    device complex128 [n_orb][n_orb] density matrix (as above)
+ *   ej_out, ek_out  host: E_J = 1/2 sum gamma_pq gamma_rs (pq|rs) and
+ *            E_K = -1/4 sum gamma_ps gamma_rq (pq|rs), reduced in FP64
+ *   cuda_stream     a cudaStream_t of the current device (NULL = default)
+ * Needs no handle and allocates nothing: its scratch is a fixed 8 MiB array in
+ * device global memory that every GPU loading the library holds until the
+ * process exits.  Limit: n_orb <= 511; larger sizes return ISDF_ERR_ARG with
+ * a message in isdf_last_error(NULL).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the array,
+ * so calls that overlap on the GPU (other streams, other threads) race; the
+ * call returns after the results are on the host. */
+int isdf_eri_traces_noalloc(const void* eri, int n_orb, const void* gamma, double* ej_out, double* ek_out,
+                            void* cuda_stream);
+
+/* Message of the last failure: of the handle h, or (h == NULL) of the last
+ * failed handle-free call on the calling thread. */
 const char* isdf_last_error(const isdf_handle* h);
 void isdf_destroy(isdf_handle* h);
 

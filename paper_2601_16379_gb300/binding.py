@@ -25,8 +25,8 @@ STATUS = {0: "ISDF_OK", -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_OOM", -3: "ISDF_ERR_CU
 # Every entry point declared in include/isdf.h.
 EXPORTS = ["isdf_create", "isdf_build_points", "isdf_set_points", "isdf_fit_zeta",
            "isdf_coulomb_metric", "isdf_fragment_eri", "isdf_get", "isdf_sizes",
-           "isdf_launch_count", "isdf_timing_enable", "isdf_timing_get", "isdf_last_error",
-           "isdf_destroy"]
+           "isdf_launch_count", "isdf_timing_enable", "isdf_timing_get", "isdf_eri_traces_noalloc",
+           "isdf_last_error", "isdf_destroy"]
 
 
 class IsdfError(RuntimeError):
@@ -68,6 +68,7 @@ def load(path: Optional[str] = None) -> ct.CDLL:
     lib.isdf_launch_count.restype = ct.c_int64
     lib.isdf_timing_enable.argtypes = [vp, ct.c_int]
     lib.isdf_timing_get.argtypes = [vp, ct.c_int, dp, ct.POINTER(ct.c_int64), dp]
+    lib.isdf_eri_traces_noalloc.argtypes = [vp, ct.c_int, vp, dp, dp, vp]
     lib.isdf_last_error.argtypes = [vp]
     lib.isdf_last_error.restype = ct.c_char_p
     lib.isdf_destroy.argtypes = [vp]
@@ -198,3 +199,14 @@ class Isdf:
         self._check(self.lib.isdf_get(self.h, int(what), _ptr(out)))
         return out
 
+
+def eri_traces_noalloc(eri, n_orb: int, gamma, stream=None):
+    """E_J, E_K of one fragment from its chemist-order ERIs, through the
+    allocation-free entry point (no handle, no device allocation)."""
+    lib = load()
+    ej, ek = ct.c_double(), ct.c_double()
+    st = ct.c_void_p(0 if stream is None else int(getattr(stream, "cuda_stream", stream)))
+    rc = lib.isdf_eri_traces_noalloc(_ptr(eri), int(n_orb), _ptr(gamma), ct.byref(ej), ct.byref(ek), st)
+    if rc != 0:
+        raise IsdfError(rc, lib.isdf_last_error(None).decode())
+    return ej.value, ek.value

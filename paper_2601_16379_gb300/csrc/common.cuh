@@ -145,6 +145,9 @@ cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale,
 cudaError_t eri_traces_f(cudaStream_t st, const float2* E, int nf, double scale,
                          const double2* gamma, double* out2);
 
+// Message of the last failed handle-free call on this thread.
+const char* noalloc_last_error();
+
 // Tensor-core E = scale * B B^H (k_tc.cu); B complex64 n2 x K with row pitch ldb,
 // E complex128 n2 x n2 (full Hermitian).  Workspace sizes from the helpers below.
 size_t herk_tc_split_bytes(int64_t n2, int64_t K);

@@ -736,7 +736,7 @@ int isdf_timing_get(const isdf_handle* h, int stage, double* ms_total, int64_t* 
   return ISDF_OK;
 }
 
-const char* isdf_last_error(const isdf_handle* h) { return h ? h->err.c_str() : "null handle"; }
+const char* isdf_last_error(const isdf_handle* h) { return h ? h->err.c_str() : isdf::noalloc_last_error(); }
 
 void isdf_destroy(isdf_handle* h) {
   if (!h) return;

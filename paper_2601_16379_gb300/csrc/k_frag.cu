@@ -7,6 +7,9 @@
 //   E_K = -1/4 sum gamma_ps gamma_rq (pq|rs)   (closed shell, spin-summed gamma).
 // The traces are reduced in FP64 with a fixed order (per-row partials, then a
 // single-block sum), so repeated calls give identical bits.
+#include <mutex>
+
+#include "../../include/isdf.h"
 #include "common.cuh"
 
 namespace isdf {
@@ -30,8 +33,9 @@ __global__ void eri_permute_kernel(const T* __restrict__ E, int nf, double scale
   }
 }
 
-// One block per (p q) row: partial J and K sums over (r, s).
-template <typename T>
+// One block per (p q) row: partial J and K sums over (r, s).  kChemist selects
+// the input layout: false reads E[(pq)][(sr)], true reads eri[p][q][r][s].
+template <typename T, bool kChemist = false>
 __global__ void __launch_bounds__(256) traces_rows_kernel(const T* __restrict__ E, int nf,
                                                           const double2* __restrict__ g,
                                                           double2* __restrict__ part) {
@@ -41,7 +45,7 @@ __global__ void __launch_bounds__(256) traces_rows_kernel(const T* __restrict__ 
   double2 aj = make_double2(0, 0), ak = make_double2(0, 0);
   for (int64_t sr = threadIdx.x; sr < n2; sr += blockDim.x) {
     const int s = (int)(sr / nf), r = (int)(sr % nf);
-    const T ev = E[pq * n2 + sr];  // = (pq|rs)
+    const T ev = kChemist ? E[pq * n2 + (int64_t)r * nf + s] : E[pq * n2 + sr];  // = (pq|rs)
     const double2 e2 = make_double2((double)ev.x, (double)ev.y);
     // J: gamma_rs * (pq|rs)
     const double2 grs = g[(int64_t)r * nf + s];
@@ -172,4 +176,68 @@ cudaError_t nonfinite_count(cudaStream_t st, const double* x, int64_t n, int32_t
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free trace entry point.  Its scratch (per-row partial sums and the
+// four result words) lives in a file-scope device array that every GPU loading
+// the library holds until the process exits; the host needs the array's device
+// address, obtained once per device with cudaGetSymbolAddress.
+namespace {
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 20;  // 8 MiB: 4 + 4*n_f^2 doubles, n_f <= 511
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+thread_local char g_noalloc_msg[256] = "";
+
+int noalloc_fail(int code, const char* msg) {
+  snprintf(g_noalloc_msg, sizeof(g_noalloc_msg), "%s", msg);
+  return code;
+}
+}  // namespace
+
+const char* noalloc_last_error() { return g_noalloc_msg; }
+
 }  // namespace isdf
+
+extern "C" int isdf_eri_traces_noalloc(const void* eri, int n_orb, const void* gamma, double* ej_out,
+                                       double* ek_out, void* cuda_stream) {
+  using namespace isdf;
+  if (!eri || !gamma || !ej_out || !ek_out || n_orb < 1)
+    return noalloc_fail(ISDF_ERR_ARG, "isdf_eri_traces_noalloc: NULL pointer or n_orb < 1");
+  const int64_t n2 = (int64_t)n_orb * n_orb;
+  if (4 + 4 * n2 > kNoAllocScratchDoubles)
+    return noalloc_fail(ISDF_ERR_ARG, "isdf_eri_traces_noalloc: n_orb exceeds the 511-orbital scratch limit");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return noalloc_fail(ISDF_ERR_CUDA, "isdf_eri_traces_noalloc: no current CUDA device");
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return noalloc_fail(ISDF_ERR_CUDA, "isdf_eri_traces_noalloc: cudaGetSymbolAddress of the scratch failed");
+      }
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  double* out = scratch;                                        // 4 result words
+  double2* part = reinterpret_cast<double2*>(scratch + 4);     // 2 * n2 partial sums
+  traces_rows_kernel<double2, true><<<(unsigned)n2, 256, 0, st>>>(static_cast<const double2*>(eri), n_orb,
+                                                                  static_cast<const double2*>(gamma), part);
+  traces_final_kernel<<<1, 256, 0, st>>>(part, n2, 1.0, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(ISDF_ERR_CUDA, cudaGetErrorString(e));
+  double hv[2];
+  e = cudaMemcpyAsync(hv, out, sizeof(hv), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return noalloc_fail(ISDF_ERR_CUDA, cudaGetErrorString(e));
+  *ej_out = hv[0];
+  *ek_out = hv[1];
+  g_noalloc_msg[0] = '\0';
+  return ISDF_OK;
+}
