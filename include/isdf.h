@@ -60,9 +60,10 @@ typedef enum {
 
 typedef enum {
   ISDF_FP64 = 0,   /* every step in FP64                                          */
-  ISDF_MIXED = 1   /* FP64 points, fit (Eqs. 3-5) and Coulomb metric (Eq. 6); the  */
-                   /* fragment pair tensor and ERI contractions (Eqs. 19-20) in    */
-                   /* reduced precision with compensated FP32 accumulation         */
+  ISDF_MIXED = 1   /* FP64 points and fit (Eqs. 3-5) and the factors of V (Eq. 6);  */
+                   /* the grid FFT and V GEMM in complex64, the fragment pair      */
+                   /* tensor and ERI contractions (Eqs. 19-20) in reduced precision */
+                   /* (compensated FP32 SIMT; exact fp16 slices on the tensor cores) */
 } isdf_precision;
 
 /* Cell, basis and sampling (Eq. 1; Section II).

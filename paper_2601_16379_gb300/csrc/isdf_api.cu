@@ -519,12 +519,22 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
   const double2* tw = (const double2*)h->buf("grid_tw");
   StageTimer stt(h, 2, 4.0 * nk * (double)np * np * ng);  // Hermitian V_xi GEMM
   ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
-  // The Coulomb metric is computed in FP64 in both precisions: V^q carries the
-  // conditioning of the fit (its scale exceeds that of the ERIs by the
-  // cancellation in M V M^H), so its rounding is kept at the FP64 level.
-  CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw));
-  CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi, ng, (int64_t)np * ng, xi, ng,
-           (int64_t)np * ng, zero, Vxi, np, (int64_t)np * np, nk));
+  if (h->prec == ISDF_FP64) {
+    CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw));
+    CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi, ng, (int64_t)np * ng, xi, ng,
+             (int64_t)np * ng, zero, Vxi, np, (int64_t)np * np, nk));
+  } else {
+    // V_xi in complex64 with compensated accumulation: xi is well scaled (|xi| ~ |rho|), and
+    // an error in V_xi reaches E as P dV_xi P^H with P = M W^T well scaled, i.e. relative to
+    // |E| (the ill-conditioned factor W is applied afterwards, in FP64).
+    ENSURE(xif, float2, "xi_f", (size_t)nk * np * ng);
+    ENSURE(Vxif, float2, "Vxi_f", (size_t)nk * np * np);
+    CK(z2c(h->st, xi, xif, (int64_t)nk * np * ng));
+    CK(grid_coulomb_fft_f(h->st, xif, np, 0, nk, h->cell, tw));
+    CK(cgemm(h->st, 'R', 'T', np, np, ng, make_float2((float)h->volume, 0.f), xif, ng, (int64_t)np * ng, xif, ng,
+             (int64_t)np * ng, make_float2(0.f, 0.f), Vxif, np, (int64_t)np * np, nk));
+    CK(c2z(h->st, Vxif, Vxi, (int64_t)nk * np * np));
+  }
   h->has_xi = false;  // xi was transformed in place (FP64) / is no longer needed
   // V_xi = L_xi L_xi^H ; L^q = W^T L_xi
   ENSURE(LtV, double2, "LtV", (size_t)nk * np * np);

@@ -243,8 +243,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    float* wh = args.ws_hi + (size_t)blockIdx.x * BN * BM;
-    float* wl = args.ws_lo + (size_t)blockIdx.x * BN * BM;
+    float* __restrict__ wh = args.ws_hi + (size_t)blockIdx.x * BN * BM;
+    float* __restrict__ wl = args.ws_lo + (size_t)blockIdx.x * BN * BM;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     for (int c = 0; c < nchunks; ++c) {
       if (!mbar_wait(accf, c & 1, s_err, args.err, 4)) break;
@@ -252,26 +252,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll 1
       for (int cb = 0; cb < BN / 32; ++cb) {
         uint32_t v0[32], v1[32], v2[32];
+        float H[32], L[32];
+        const size_t base = (size_t)(cb * 32) * BM + row;
+        if (c > 0) {
+          // issue all 64 global loads of this column block before the TMEM reads
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            H[j] = wh[base + (size_t)j * BM];
+            L[j] = wl[base + (size_t)j * BM];
+          }
+        }
         tmem_ld32(tmem_base + lane_off + (uint32_t)(cb * 32), v0);
         tmem_ld32(tmem_base + lane_off + (uint32_t)(BN + cb * 32), v1);
         tmem_ld32(tmem_base + lane_off + (uint32_t)(2 * BN + cb * 32), v2);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const size_t idx = (size_t)(cb * 32 + j) * BM + row;
           const float a0 = __uint_as_float(v0[j]);
           const float t = fmaf(__uint_as_float(v2[j]), 1.0f / 16384.0f, __uint_as_float(v1[j]) * (1.0f / 128.0f));
           if (c == 0) {
-            wh[idx] = a0;
-            wl[idx] = t;
+            H[j] = a0;
+            L[j] = t;
           } else {
             // (H, L) += (a0, t) with TwoSum on the high parts
-            const float H = wh[idx];
-            const float S = H + a0;
-            const float bp = S - H;
-            const float e = (H - (S - bp)) + (a0 - bp);
-            wh[idx] = S;
-            wl[idx] = wl[idx] + (e + t);
+            const float S = H[j] + a0;
+            const float bp = S - H[j];
+            const float e = (H[j] - (S - bp)) + (a0 - bp);
+            H[j] = S;
+            L[j] = L[j] + (e + t);
           }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          wh[base + (size_t)j * BM] = H[j];
+          wl[base + (size_t)j * BM] = L[j];
         }
       }
       tc_fence_before();
