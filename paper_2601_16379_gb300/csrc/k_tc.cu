@@ -15,11 +15,14 @@
 // stored as fp16 (exact).  The tcgen05.mma kind::f16 products of integer
 // slices are integers, and the three weight groups
 //     g0 = S1.T1,  g1 = S1.T2 + S2.T1,  g2 = S1.T3 + S2.T2 + S3.T1
-// are accumulated in three FP32 TMEM accumulators.  A chunk of at most 48
-// k-steps keeps every partial sum an integer below 2^24, so the FP32
-// accumulation is exact whatever its rounding; after each chunk the epilogue
-// adds (g0, g1/128 + g2/128^2) into a float-float (TwoSum) accumulator in
-// global memory.  The result is accurate to ~2^-22 of |B_a||B_b| and unbiased.
+// are accumulated in FP32 TMEM.  g0 carries weight 1 and must be exact: a
+// chunk of 48 k-steps keeps its partial sums integers below 2^24, so the FP32
+// accumulation is exact whatever its rounding; g0 is double-buffered and each
+// chunk is drained (overlapping the next chunk's MMAs) into a float-float
+// (TwoSum) accumulator in global memory.  g1 and g2 carry weights 2^-7 and
+// 2^-14, so the truncation of tcgen05's FP32 accumulation over longer runs
+// enters only scaled down: they are drained every 4 and 16 chunks (bias below
+// 1e-7 of |B_a||B_b|).  The result is accurate to ~2^-22 of |B_a||B_b|.
 //
 // Kernel roles (192 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
 // and issues the MMAs, warps 2-5 drain TMEM into the float-float workspace.
@@ -44,9 +47,11 @@ constexpr int NSLICE = 3;
 constexpr int A_BYTES = BM * BK * 2;        // 16 KB per slice
 constexpr int B_BYTES = BN * BK * 2;        // 16 KB per slice
 constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);  // 96 KB
-constexpr int TMEM_COLS = 512;              // three 128-column FP32 accumulators (power-of-two allocation)
+constexpr int TMEM_COLS = 512;              // g0 (two buffers), g1, g2: four 128-column FP32 accumulators
 constexpr int NTHREADS = 192;
-constexpr int kChunkKB = 12;                // k-blocks per exact chunk: 48 k-steps of 16
+constexpr int kChunkKB = 12;                // k-blocks per exact g0 chunk: 48 k-steps of 16
+constexpr int kP1 = 4;                      // chunks per g1 drain
+constexpr int kP2 = 16;                     // chunks per g2 drain
 constexpr unsigned long long kWaitNs = 4000000000ULL;  // bounded waits: 4 s of device time
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -155,9 +160,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* full = bars;                   // [STAGES]
   uint64_t* empty = bars + STAGES;         // [STAGES]
-  uint64_t* accf = bars + 2 * STAGES;      // chunk accumulated
-  uint64_t* acce = bars + 2 * STAGES + 1;  // chunk drained
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  uint64_t* accf = bars + 2 * STAGES;      // [2] chunk accumulated (per g0 buffer)
+  uint64_t* acce = bars + 2 * STAGES + 2;  // [2] g0 buffer drained
+  uint64_t* acce1 = bars + 2 * STAGES + 4; // g1 drained
+  uint64_t* acce2 = bars + 2 * STAGES + 5; // g2 drained
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
   volatile int* s_err = reinterpret_cast<volatile int*>(s_tmem + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -170,8 +177,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
-    mbar_init(acce, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
+    mbar_init(acce1, 128);
+    mbar_init(acce2, 128);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -209,9 +220,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = kb % STAGES, r = kb / STAGES;
         const int c = kb / kChunkKB;
         const bool first_in_chunk = (kb % kChunkKB) == 0;
-        if (first_in_chunk && c > 0) {
-          // the epilogue must have drained the previous chunk
-          if (!mbar_wait(acce, (c - 1) & 1, s_err, args.err, 2)) break;
+        const bool reset1 = first_in_chunk && (c % kP1) == 0;
+        const bool reset2 = first_in_chunk && (c % kP2) == 0;
+        if (first_in_chunk) {
+          bool ok = true;
+          // g0 buffer (c & 1) was last used by chunk c - 2
+          if (c >= 2) ok = mbar_wait(&acce[c & 1], ((c >> 1) - 1) & 1, s_err, args.err, 2);
+          if (ok && reset1 && c > 0) ok = mbar_wait(acce1, ((c / kP1) - 1) & 1, s_err, args.err, 5);
+          if (ok && reset2 && c > 0) ok = mbar_wait(acce2, ((c / kP2) - 1) & 1, s_err, args.err, 6);
+          if (!ok) break;
           tc_fence_after();
         }
         if (!mbar_wait(&full[s], r & 1, s_err, args.err, 3)) break;
@@ -223,20 +240,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           dA[i] = sdesc_sw128(st + i * A_BYTES);
           dB[i] = sdesc_sw128(st + NSLICE * A_BYTES + i * B_BYTES);
         }
-        const uint32_t g0 = tmem_base, g1 = tmem_base + BN, g2 = tmem_base + 2 * BN;
+        const uint32_t g0 = tmem_base + (uint32_t)((c & 1) * BN), g1 = tmem_base + 2 * BN,
+                       g2 = tmem_base + 3 * BN;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 fp16 = 32 bytes along K
-          const uint32_t acc = (first_in_chunk && kk == 0) ? 0u : 1u;
-          umma_f16(g0, dA[0] + off, dB[0] + off, kIdesc, acc);
-          umma_f16(g1, dA[0] + off, dB[1] + off, kIdesc, acc);
+          const uint32_t a0 = (first_in_chunk && kk == 0) ? 0u : 1u;
+          const uint32_t a1 = (reset1 && kk == 0) ? 0u : 1u;
+          const uint32_t a2 = (reset2 && kk == 0) ? 0u : 1u;
+          umma_f16(g0, dA[0] + off, dB[0] + off, kIdesc, a0);
+          umma_f16(g1, dA[0] + off, dB[1] + off, kIdesc, a1);
           umma_f16(g1, dA[1] + off, dB[0] + off, kIdesc, 1u);
-          umma_f16(g2, dA[0] + off, dB[2] + off, kIdesc, acc);
+          umma_f16(g2, dA[0] + off, dB[2] + off, kIdesc, a2);
           umma_f16(g2, dA[1] + off, dB[1] + off, kIdesc, 1u);
           umma_f16(g2, dA[2] + off, dB[0] + off, kIdesc, 1u);
         }
         umma_commit(&empty[s]);
-        if ((kb % kChunkKB) == kChunkKB - 1 || kb == nkb - 1) umma_commit(accf);
+        if ((kb % kChunkKB) == kChunkKB - 1 || kb == nkb - 1) umma_commit(&accf[c & 1]);
       }
     }
   } else {
@@ -247,11 +267,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float* __restrict__ wl = args.ws_lo + (size_t)blockIdx.x * BN * BM;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     for (int c = 0; c < nchunks; ++c) {
-      if (!mbar_wait(accf, c & 1, s_err, args.err, 4)) break;
+      if (!mbar_wait(&accf[c & 1], (c >> 1) & 1, s_err, args.err, 4)) break;
       tc_fence_after();
+      const bool last = (c == nchunks - 1);
+      const bool drain1 = last || (c % kP1) == kP1 - 1;
+      const bool drain2 = last || (c % kP2) == kP2 - 1;
 #pragma unroll 1
       for (int cb = 0; cb < BN / 32; ++cb) {
-        uint32_t v0[32], v1[32], v2[32];
+        uint32_t v0[32];
         float H[32], L[32];
         const size_t base = (size_t)(cb * 32) * BM + row;
         if (c > 0) {
@@ -262,24 +285,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             L[j] = wl[base + (size_t)j * BM];
           }
         }
-        tmem_ld32(tmem_base + lane_off + (uint32_t)(cb * 32), v0);
-        tmem_ld32(tmem_base + lane_off + (uint32_t)(BN + cb * 32), v1);
-        tmem_ld32(tmem_base + lane_off + (uint32_t)(2 * BN + cb * 32), v2);
+        tmem_ld32(tmem_base + lane_off + (uint32_t)((c & 1) * BN + cb * 32), v0);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float a0 = __uint_as_float(v0[j]);
-          const float t = fmaf(__uint_as_float(v2[j]), 1.0f / 16384.0f, __uint_as_float(v1[j]) * (1.0f / 128.0f));
           if (c == 0) {
             H[j] = a0;
-            L[j] = t;
+            L[j] = 0.f;
           } else {
-            // (H, L) += (a0, t) with TwoSum on the high parts
+            // (H, L) += a0 with TwoSum on the high part
             const float S = H[j] + a0;
             const float bp = S - H[j];
             const float e = (H[j] - (S - bp)) + (a0 - bp);
             H[j] = S;
-            L[j] = L[j] + (e + t);
+            L[j] += e;
           }
+        }
+        if (drain1) {
+          uint32_t v1[32];
+          tmem_ld32(tmem_base + lane_off + (uint32_t)(2 * BN + cb * 32), v1);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) L[j] = fmaf(__uint_as_float(v1[j]), 1.0f / 128.0f, L[j]);
+        }
+        if (drain2) {
+          uint32_t v2[32];
+          tmem_ld32(tmem_base + lane_off + (uint32_t)(3 * BN + cb * 32), v2);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) L[j] = fmaf(__uint_as_float(v2[j]), 1.0f / 16384.0f, L[j]);
         }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -288,7 +320,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(acce);
+      mbar_arrive(&acce[c & 1]);
+      if (drain1) mbar_arrive(acce1);
+      if (drain2) mbar_arrive(acce2);
     }
   }
   tc_fence_before();
