@@ -126,11 +126,13 @@ cudaError_t lt_to_rowmajor(cudaStream_t st, const double2* Lt, const int32_t* ra
 
 // Grid FFT of rows x[q][I][r] (complex128), in place:
 //   x <- sqrt(w(q+G)) * (1/N_g) FFT(e^{-i q.r} x)   with w = 4 pi/|q+G|^2, 0 at q+G = 0.
-// dtw: device table of 3 x 64 forward twiddles exp(-2 pi i j/n_a) (grid_twiddles).
+// dtw: device table of 3 x 64 forward twiddles exp(-2 pi i j/n_a) (grid_twiddles);
+// work: grid_coulomb_work_bytes(nq) bytes of device scratch (phase and weight tables).
+size_t grid_coulomb_work_bytes(int nq, const CellDev& c);
 cudaError_t grid_coulomb_fft(cudaStream_t st, double2* x, int rows_per_q, int q0, int nq,
-                             const CellDev& c, const double2* dtw);
+                             const CellDev& c, const double2* dtw, void* work);
 cudaError_t grid_coulomb_fft_f(cudaStream_t st, float2* x, int rows_per_q, int q0, int nq,
-                               const CellDev& c, const double2* dtw);
+                               const CellDev& c, const double2* dtw, void* work);
 void grid_twiddles(const int mesh[3], double2* host192);
 
 // Fragment pair products Z[R][(p q)][I] = conj(t[R][I][p]) * t[R][I][q].

@@ -519,8 +519,9 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
   const double2* tw = (const double2*)h->buf("grid_tw");
   StageTimer stt(h, 2, 4.0 * nk * (double)np * np * ng);  // Hermitian V_xi GEMM
   ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
+  ENSURE(gwork, uint8_t, "grid_work", grid_coulomb_work_bytes(nk, h->cell));
   if (h->prec == ISDF_FP64) {
-    CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw));
+    CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw, gwork));
     CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi, ng, (int64_t)np * ng, xi, ng,
              (int64_t)np * ng, zero, Vxi, np, (int64_t)np * np, nk));
   } else {
@@ -530,7 +531,7 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
     ENSURE(xif, float2, "xi_f", (size_t)nk * np * ng);
     ENSURE(Vxif, float2, "Vxi_f", (size_t)nk * np * np);
     CK(z2c(h->st, xi, xif, (int64_t)nk * np * ng));
-    CK(grid_coulomb_fft_f(h->st, xif, np, 0, nk, h->cell, tw));
+    CK(grid_coulomb_fft_f(h->st, xif, np, 0, nk, h->cell, tw, gwork));
     CK(cgemm(h->st, 'R', 'T', np, np, ng, make_float2((float)h->volume, 0.f), xif, ng, (int64_t)np * ng, xif, ng,
              (int64_t)np * ng, make_float2(0.f, 0.f), Vxif, np, (int64_t)np * np, nk));
     CK(c2z(h->st, Vxif, Vxi, (int64_t)nk * np * np));

@@ -49,8 +49,10 @@ Twiddles16 make_tw(const int n[3], int sign) {
 }
 
 // In-place DFT along the three k-mesh axes of s[k][c] (Nk x ct), line per thread.
+// tc/ts: twiddle cos/sin tables [3][16] in the working precision (shared memory).
 template <typename T>
-__device__ void kmesh_dft_smem(T* s, int ct, const int n[3], const Twiddles16& tw) {
+__device__ void kmesh_dft_smem(T* s, int ct, const int n[3], const typename CT<T>::R* tc,
+                               const typename CT<T>::R* ts) {
   using R = typename CT<T>::R;
   const int nk = n[0] * n[1] * n[2];
   for (int a = 2; a >= 0; --a) {
@@ -76,7 +78,7 @@ __device__ void kmesh_dft_smem(T* s, int ct, const int n[3], const Twiddles16& t
         for (int i = 0; i < 16; ++i) {
           if (i >= L) break;
           const int t = (i * j) % L;
-          const R cr = (R)tw.c[a][t], ci = (R)tw.s[a][t];
+          const R cr = tc[a * 16 + t], ci = ts[a * 16 + t];
           ax += v[i].x * cr - v[i].y * ci;
           ay += v[i].x * ci + v[i].y * cr;
         }
@@ -91,8 +93,16 @@ template <typename T>
 __global__ void __launch_bounds__(256) kdft_cols_kernel(T* __restrict__ data, int64_t ncol, KMesh km,
                                                         int ct, int mode, Twiddles16 tw1,
                                                         Twiddles16 tw2, double scale) {
+  using R = typename CT<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
+  __shared__ R tw1c[48], tw1s[48], tw2c[48], tw2s[48];
+  for (int t = threadIdx.x; t < 48; t += blockDim.x) {
+    tw1c[t] = (R)tw1.c[t / 16][t % 16];
+    tw1s[t] = (R)tw1.s[t / 16][t % 16];
+    tw2c[t] = (R)tw2.c[t / 16][t % 16];
+    tw2s[t] = (R)tw2.s[t / 16][t % 16];
+  }
   const int nk = km.n[0] * km.n[1] * km.n[2];
   const int64_t c0 = (int64_t)blockIdx.x * ct;
   for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
@@ -103,16 +113,15 @@ __global__ void __launch_bounds__(256) kdft_cols_kernel(T* __restrict__ data, in
     s[e] = v;
   }
   __syncthreads();
-  kmesh_dft_smem<T>(s, ct, km.n, tw1);
+  kmesh_dft_smem<T>(s, ct, km.n, tw1c, tw1s);
   if (mode == 1) {
     for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
       T v = s[e];
       s[e] = CT<T>::mk(v.x * v.x + v.y * v.y, 0);
     }
     __syncthreads();
-    kmesh_dft_smem<T>(s, ct, km.n, tw2);
+    kmesh_dft_smem<T>(s, ct, km.n, tw2c, tw2s);
   }
-  using R = typename CT<T>::R;
   for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
     const int k = e / ct, c = e % ct;
     const int64_t col = c0 + c;
@@ -154,11 +163,29 @@ struct GridFFTParams {
   double rec[9];
 };
 
-// x[row][r] *= exp(-i q.r), q = sum_a m_a/nk_a b_a  (rows grouped by q)
+// Per-axis phase table: ph[a][m][g] = exp(-2 pi i m g / (nk_a n_a)), m < 16, g < 64.
+__global__ void phase_table_kernel(GridFFTParams p, double2* __restrict__ ph) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 3 * 16 * 64; e += gridDim.x * blockDim.x) {
+    const int a = e / 1024, m = (e / 64) % 16, g = e % 64;
+    double2 v = make_double2(1.0, 0.0);
+    if (m < p.kmesh[a] && g < p.n[a]) {
+      const int den = p.kmesh[a] * p.n[a];
+      double sn, cs;
+      sincospi(-2.0 * (double)((m * g) % den) / (double)den, &sn, &cs);
+      v = make_double2(cs, sn);
+    }
+    ph[e] = v;
+  }
+}
+
+// x[row][r] *= exp(-i q.r) = ph[0][m0][g0] ph[1][m1][g1] ph[2][m2][g2]  (rows grouped by q)
 template <typename T>
-__global__ void phase_kernel(T* __restrict__ x, int64_t rows_per_q, int q0, int nq,
-                             GridFFTParams p) {
+__global__ void phase_kernel(T* __restrict__ x, int64_t rows_per_q, int q0, int nq, GridFFTParams p,
+                             const double2* __restrict__ ph) {
   using R = typename CT<T>::R;
+  __shared__ T sph[3 * 16 * 64];
+  for (int e = threadIdx.x; e < 3 * 16 * 64; e += blockDim.x) sph[e] = CT<T>::mk((R)ph[e].x, (R)ph[e].y);
+  __syncthreads();
   const int ng = p.n[0] * p.n[1] * p.n[2];
   const int64_t total = (int64_t)nq * rows_per_q * ng;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -168,14 +195,8 @@ __global__ void phase_kernel(T* __restrict__ x, int64_t rows_per_q, int q0, int 
     const int q = q0 + qi;
     const int m2 = q % p.kmesh[2], m1 = (q / p.kmesh[2]) % p.kmesh[1], m0 = q / (p.kmesh[1] * p.kmesh[2]);
     const int g2 = r % p.n[2], g1 = (r / p.n[2]) % p.n[1], g0 = r / (p.n[1] * p.n[2]);
-    // fraction of a full turn, reduced exactly per axis
-    const double f = (double)((m0 * g0) % (p.kmesh[0] * p.n[0])) / (double)(p.kmesh[0] * p.n[0]) +
-                     (double)((m1 * g1) % (p.kmesh[1] * p.n[1])) / (double)(p.kmesh[1] * p.n[1]) +
-                     (double)((m2 * g2) % (p.kmesh[2] * p.n[2])) / (double)(p.kmesh[2] * p.n[2]);
-    double sn, cs;
-    sincospi(-2.0 * (f - floor(f)), &sn, &cs);
-    T v = x[e];
-    x[e] = CT<T>::mk(v.x * (R)cs - v.y * (R)sn, v.x * (R)sn + v.y * (R)cs);
+    const T f = cmul(cmul(sph[m0 * 64 + g0], sph[1024 + m1 * 64 + g1]), sph[2048 + m2 * 64 + g2]);
+    x[e] = cmul(x[e], f);
   }
 }
 
@@ -187,12 +208,12 @@ __global__ void __launch_bounds__(256) grid_axis_kernel(T* __restrict__ x, int64
                                                         const double2* __restrict__ tw) {
   using R = typename CT<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* tws = reinterpret_cast<double2*>(smem_raw);  // 64 entries, 16-byte aligned
+  T* tws = reinterpret_cast<T*>(smem_raw);  // 64 twiddles in the working precision
   T* s = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double2));
   const int64_t lines_per_row = ng / L;
   const int64_t total_lines = nrows * lines_per_row;
   const int64_t l0 = (int64_t)blockIdx.x * lpb;
-  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = tw[t];
+  for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = CT<T>::mk((R)tw[t].x, (R)tw[t].y);
   // line id -> base element offset
   auto base_of = [&](int64_t line) -> int64_t {
     const int64_t row = line / lines_per_row;
@@ -230,10 +251,10 @@ __global__ void __launch_bounds__(256) grid_axis_kernel(T* __restrict__ x, int64
     R ax = 0, ay = 0;
     int t = 0;
     for (int i = 0; i < L; ++i) {
-      const double2 w = tws[t];
+      const T w = tws[t];
       const T v = sl[i];
-      ax += v.x * (R)w.x - v.y * (R)w.y;
-      ay += v.x * (R)w.y + v.y * (R)w.x;
+      ax += v.x * w.x - v.y * w.y;
+      ay += v.x * w.y + v.y * w.x;
       t += j;
       if (t >= L) t -= L;
       if (t >= L) t %= L;
@@ -242,17 +263,14 @@ __global__ void __launch_bounds__(256) grid_axis_kernel(T* __restrict__ x, int64
   }
 }
 
-// x[row][G] *= sqrt(w(q+G)) / N_g
-template <typename T>
-__global__ void coulomb_weight_kernel(T* __restrict__ x, int64_t rows_per_q, int q0, int nq,
-                                      GridFFTParams p) {
-  using R = typename CT<T>::R;
+// sw[qi][G] = sqrt(4 pi / |q+G|^2) / N_g  (0 at q+G = 0)
+__global__ void weight_table_kernel(int q0, int nq, GridFFTParams p, double* __restrict__ sw) {
   const int ng = p.n[0] * p.n[1] * p.n[2];
-  const int64_t total = (int64_t)nq * rows_per_q * ng;
+  const int64_t total = (int64_t)nq * ng;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int h = (int)(e % ng);
-    const int q = q0 + (int)(e / ((int64_t)rows_per_q * ng));
+    const int q = q0 + (int)(e / ng);
     const int m2 = q % p.kmesh[2], m1 = (q / p.kmesh[2]) % p.kmesh[1], m0 = q / (p.kmesh[1] * p.kmesh[2]);
     const int h2 = h % p.n[2], h1 = (h / p.n[2]) % p.n[1], h0 = h / (p.n[1] * p.n[2]);
     const int hh[3] = {h0, h1, h2};
@@ -267,16 +285,30 @@ __global__ void coulomb_weight_kernel(T* __restrict__ x, int64_t rows_per_q, int
       const double comp = fr[0] * p.rec[0 * 3 + c] + fr[1] * p.rec[1 * 3 + c] + fr[2] * p.rec[2 * 3 + c];
       v2 += comp * comp;
     }
-    const bool zero = (mm[0] == 0 && mm[1] == 0 && mm[2] == 0 && fr[0] == 0 && fr[1] == 0 && fr[2] == 0);
-    const double sw = zero ? 0.0 : sqrt(4.0 * M_PI / v2) / (double)ng;
+    const bool zero = (fr[0] == 0 && fr[1] == 0 && fr[2] == 0);
+    sw[e] = zero ? 0.0 : sqrt(4.0 * M_PI / v2) / (double)ng;
+  }
+}
+
+// x[qi][I][G] *= sw[qi][G]
+template <typename T>
+__global__ void coulomb_weight_kernel(T* __restrict__ x, int64_t rows_per_q, int nq, int ng,
+                                      const double* __restrict__ sw) {
+  using R = typename CT<T>::R;
+  const int64_t total = (int64_t)nq * rows_per_q * ng;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(e % ng);
+    const int64_t qi = e / ((int64_t)rows_per_q * ng);
+    const R w = (R)sw[qi * ng + h];
     T v = x[e];
-    x[e] = CT<T>::mk(v.x * (R)sw, v.y * (R)sw);
+    x[e] = CT<T>::mk(v.x * w, v.y * w);
   }
 }
 
 template <typename T>
 cudaError_t grid_fft_launch(cudaStream_t st, T* x, int rows_per_q, int q0, int nq, const CellDev& c,
-                            const double2* dtw) {
+                            const double2* dtw, void* work) {
   GridFFTParams p;
   for (int a = 0; a < 3; ++a) {
     p.n[a] = c.mesh[a];
@@ -290,8 +322,18 @@ cudaError_t grid_fft_launch(cudaStream_t st, T* x, int rows_per_q, int q0, int n
   const int64_t total = nrows * ng;
   int nb = (int)((total + 255) / 256);
   if (nb > 152 * 64) nb = 152 * 64;
-  phase_kernel<T><<<nb, 256, 0, st>>>(x, rows_per_q, q0, nq, p);
+  double2* ph = reinterpret_cast<double2*>(work);            // 3 x 16 x 64 phase table
+  double* sw = reinterpret_cast<double*>(ph + 3 * 16 * 64);   // nq x ng weight table
+  phase_table_kernel<<<12, 256, 0, st>>>(p, ph);
   count_launch();
+  phase_kernel<T><<<nb, 256, 0, st>>>(x, rows_per_q, q0, nq, p, ph);
+  count_launch();
+  {
+    int nbw = (int)(((int64_t)nq * ng + 255) / 256);
+    if (nbw > 152 * 64) nbw = 152 * 64;
+    weight_table_kernel<<<nbw, 256, 0, st>>>(q0, nq, p, sw);
+    count_launch();
+  }
   for (int a = 2; a >= 0; --a) {
     const int L = c.mesh[a];
     if (L == 1) continue;
@@ -304,7 +346,7 @@ cudaError_t grid_fft_launch(cudaStream_t st, T* x, int rows_per_q, int q0, int n
     grid_axis_kernel<T><<<(unsigned)nblk, 256, smem, st>>>(x, nrows, ng, L, S, lpb, dtw + a * 64);
     count_launch();
   }
-  coulomb_weight_kernel<T><<<nb, 256, 0, st>>>(x, rows_per_q, q0, nq, p);
+  coulomb_weight_kernel<T><<<nb, 256, 0, st>>>(x, rows_per_q, nq, ng, sw);
   count_launch();
   return cudaGetLastError();
 }
@@ -339,13 +381,16 @@ cudaError_t kdft_cols_f(cudaStream_t st, float2* data, int64_t ncol, KMesh km, i
                         int mode, float scale) {
   return kdft_launch<float2>(st, data, ncol, km, s1, s2, mode, scale);
 }
+size_t grid_coulomb_work_bytes(int nq, const CellDev& c) {
+  return 3 * 16 * 64 * sizeof(double2) + (size_t)nq * c.mesh[0] * c.mesh[1] * c.mesh[2] * sizeof(double);
+}
 cudaError_t grid_coulomb_fft(cudaStream_t st, double2* x, int rows_per_q, int q0, int nq,
-                             const CellDev& c, const double2* dtw) {
-  return grid_fft_launch<double2>(st, x, rows_per_q, q0, nq, c, dtw);
+                             const CellDev& c, const double2* dtw, void* work) {
+  return grid_fft_launch<double2>(st, x, rows_per_q, q0, nq, c, dtw, work);
 }
 cudaError_t grid_coulomb_fft_f(cudaStream_t st, float2* x, int rows_per_q, int q0, int nq,
-                               const CellDev& c, const double2* dtw) {
-  return grid_fft_launch<float2>(st, x, rows_per_q, q0, nq, c, dtw);
+                               const CellDev& c, const double2* dtw, void* work) {
+  return grid_fft_launch<float2>(st, x, rows_per_q, q0, nq, c, dtw, work);
 }
 
 void grid_twiddles(const int mesh[3], double2* host192) {
