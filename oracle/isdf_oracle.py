@@ -26,9 +26,11 @@ Steps and the passages they follow
 * ``rhs_eta``        Eq. 5 (the right-hand side eta^q).
 * ``fit_zeta``       Eq. 3 (Pi^q xi^q = eta^q) solved by pivoted Cholesky.
 * ``coulomb_metric`` Eq. 6 (Coulomb kernel of the interpolation functions).
+* ``coulomb_metric_eta``  Eqs. 7-8 (the same kernel from eta, without zeta).
 * ``fragment_T``, ``pair_tensor``  Eq. 20 and Algorithm 2 (the R^q intermediate).
 * ``fragment_eri``   Eq. 19 (fragment ERIs from R^q and W^q).
 * ``traces``         Coulomb / exchange energy traces of the fragment ERIs.
+* ``exchange_matrix`` Eq. 10 (k-point exchange matrix from the ISDF integrals).
 
 Readings of the paper used here (the paper is silent or ambiguous):
 * The least-squares index placement of Eqs. 4-5 is taken as the normal
@@ -57,6 +59,7 @@ __all__ = [
     "coulomb_metric", "fragment_T", "pair_tensor", "fragment_E", "eri_from_E",
     "fragment_eri", "traces", "cheap_J", "run_isdf", "fftdf_fragment_eri",
     "supercell", "supercell_coefficients", "supercell_ips", "TIE_EPS", "LATTICE_EXP_CUT",
+    "pinv_pchol", "coulomb_metric_eta", "exchange_matrix", "fftdf_exchange_matrix",
 ]
 
 # exp(-40) tail rule of the lattice sum (Eq. 1): images whose Gaussian factor
@@ -397,6 +400,36 @@ def coulomb_metric(cell, zeta: np.ndarray, qs: Sequence[int]) -> np.ndarray:
     return np.array(out)
 
 
+def pinv_pchol(A: np.ndarray, tol: float) -> np.ndarray:
+    """Basic pseudo-inverse from the pivoted Cholesky: A^+ = P_S (A_SS)^{-1} P_S^T,
+    zero outside the kept pivots S (the same truncation as the solve of Eq. 3)."""
+    L, perm, r = pchol(A, tol)
+    out = np.zeros_like(A)
+    if r:
+        Ls = L[perm, :r]
+        inv = sla.solve_triangular(Ls, np.eye(r, dtype=A.dtype), lower=True)
+        out[np.ix_(perm, perm)] = inv.conj().T @ inv
+    return out
+
+
+def coulomb_metric_eta(cell, Pi: np.ndarray, eta: np.ndarray, solve_tol: float,
+                       qs: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Coulomb kernel without forming zeta (Eqs. 7-8): V^q from the fitting
+    right-hand side eta^q (Eq. 7, the same integral as Eq. 6 with eta in place of
+    xi), then the least-squares solution of Pi W Pi = V (Eq. 8) through the
+    truncated pseudo-inverse of the solve: W = conj(Pi^+) V conj(Pi^+).  The
+    conjugates follow from zeta = Pi^+ eta with the Hermitian Pi of Eq. 4 in the
+    index placement used here (Eq. 8 reads Pi^T W Pi^T = V in that placement)."""
+    nk = Pi.shape[0]
+    qs = list(range(nk)) if qs is None else list(qs)
+    Veta = coulomb_metric(cell, eta, qs)
+    out = []
+    for i, q in enumerate(qs):
+        P = pinv_pchol(Pi[q], solve_tol).conj()
+        out.append(P @ Veta[i] @ P)
+    return np.array(out)
+
+
 # ----------------------------------------------------------------------------
 # Fragment ERIs (Eqs. 17-20, Algorithm 2)
 # ----------------------------------------------------------------------------
@@ -463,6 +496,64 @@ def cheap_J(M: np.ndarray, V: np.ndarray, gamma: np.ndarray, nk: int) -> float:
         tot += a @ V[i] @ a.conj()
     return float((tot / (2.0 * nk)).real)
 
+
+# ----------------------------------------------------------------------------
+# k-point exchange matrix (Eq. 10)
+# ----------------------------------------------------------------------------
+
+def exchange_matrix(X: np.ndarray, V: np.ndarray, P: np.ndarray, kmesh: Sequence[int]) -> np.ndarray:
+    """K^k_{mu nu} = -(1/Nk) sum_{k'} sum_{lam sig} P^{k'}_{lam sig} (mu k, lam k' | sig k', nu k)
+    with the ISDF integrals (Eq. 9), by the direct k-sum of Eq. 10:
+
+      rho^{k'}_{IJ} = sum_{lam sig} X^{k'}_{I lam} P^{k'}_{lam sig} conj(X^{k'}_{J sig}),
+      Gamma^k_{IJ}  = sum_{k'} V^{k'-k}_{JI} rho^{k'}_{IJ},
+      K^k = -(1/Nk) X^k^H Gamma^k X^k.
+
+    P is the AO density matrix per k with the density sum_{k lam sig}
+    Phi^k_lam(r) P^k_{lam sig} conj(Phi^k_sig(r)) / Nk."""
+    nk = X.shape[0]
+    km = k_minus_table(kmesh)
+    rho = np.einsum("kil,kls,kjs->kij", X, P, X.conj())
+    out = []
+    for k in range(nk):
+        G = np.zeros(rho.shape[1:], np.complex128)
+        for kp in range(nk):
+            G += V[km[kp, k]].T * rho[kp]
+        out.append(-(X[k].conj().T @ G @ X[k]) / nk)
+    return np.array(out)
+
+
+def fftdf_exchange_matrix(cell, P: np.ndarray, phi: Optional[np.ndarray] = None) -> np.ndarray:
+    """Grid-exact exchange (no density fitting): for each k, k' the pair densities
+    conj(Phi^k_mu) Phi^{k'}_lam (momentum k' - k) are Poisson-solved on the cell grid
+    with the weights 4 pi/|q+G|^2 (q+G = 0 dropped) and contracted as in Eq. 10."""
+    if phi is None:
+        phi = bloch_ao(cell)
+    nk, nao, ng = phi.shape
+    km = k_minus_table(cell.kmesh)
+    mesh = tuple(cell.mesh)
+    gi = grid_index_vectors(mesh).astype(np.float64)
+    mk = kmesh_indices(cell.kmesh).astype(np.float64)
+    den = (np.asarray(cell.kmesh, np.float64) * np.asarray(mesh, np.float64))[None, :]
+    K = np.zeros((nk, nao, nao), np.complex128)
+    for k in range(nk):
+        for kp in range(nk):
+            q = km[kp, k]
+            # rho_{mu lam}(r) = conj(Phi^k_mu) Phi^{k'}_lam, Bloch with momentum q = k' - k
+            rho = (phi[k].conj()[:, None, :] * phi[kp][None, :, :]).reshape(nao * nao, ng)
+            u = rho * np.exp(-2j * math.pi * np.sum(mk[q][None, :] * gi / den, axis=1))[None, :]
+            c = np.fft.fftn(u.reshape((-1,) + mesh), axes=(1, 2, 3)).reshape(nao * nao, ng) / ng
+            qg = gvectors_q(cell, q)
+            g2 = np.einsum("ij,ij->i", qg, qg)
+            w = np.zeros(ng)
+            nz = g2 > 1e-300
+            w[nz] = 4.0 * math.pi / g2[nz]
+            # V4[mu][lam][nu][sig] = int conj(rho_{mu lam}) v rho_{nu sig}; the second density of
+            # (mu k lam k' | sig k' nu k) is conj(rho_{nu sig}), so that integral is conj(V4)
+            Vmat = cell.volume * (c.conj() * w[None, :]) @ c.T
+            V4 = Vmat.reshape(nao, nao, nao, nao)
+            K[k] += -np.einsum("ls,mlns->mn", P[kp], V4.conj()) / nk
+    return K
 
 # ----------------------------------------------------------------------------
 # Whole path

@@ -235,6 +235,26 @@ def test_coulomb_hermitian_psd(c1run):
         assert np.allclose(r["V"][km[0, q]], V.conj(), atol=1e-11 * s)
 
 
+def test_eta_route_equals_zeta_route(tiny5):
+    """Eqs. 7-8 (Coulomb matrix of eta, then Pi W Pi = V) give the same fragment
+    ERIs as Eq. 6 applied to the solved zeta, for the same truncation.  The
+    eta route multiplies rounding by cond(Pi) instead of its square root, so
+    the routes are compared at tau = 1e-8 (5e-6 apart at tau = 1e-12 on this
+    fit, whose condition number is 7e8); a sign or conjugation error in Eq. 8
+    moves them apart by orders of magnitude."""
+    cell, phi, ips, nf = tiny5
+    X = O.interp_vectors(phi, ips)
+    Pi = O.metric_pi(X, cell.kmesh)
+    eta = O.rhs_eta(X, phi, cell.kmesh)
+    zeta, _ = O.fit_zeta(Pi, eta, 1e-8)
+    V = O.coulomb_metric(cell, zeta, range(cell.nkpts))
+    Wq = O.coulomb_metric_eta(cell, Pi, eta, 1e-8)
+    f = W.make_fragment(cell, 5, 0, 4)
+    e1 = O.fragment_eri(X, V, f.C, cell.kmesh)
+    e2 = O.fragment_eri(X, Wq, f.C, cell.kmesh)
+    assert np.abs(e1 - e2).max() < 1e-7 * np.abs(e1).max()
+
+
 # ---------------------------------------------------------- end-to-end pins
 def test_isdf_exact_limit_and_convergence(tiny):
     """With N_P at the pair-space rank the ISDF ERIs equal the grid-exact
@@ -264,6 +284,39 @@ def test_gamma_supercell_equivalence(tiny5):
     rs = O.run_isdf(sc, cell.nkpts * n_p, 0, solve_tol=1e-14, ips=O.supercell_ips(cell, ips[:n_p]))
     eri_g = O.fragment_eri(rs["X"], rs["V"], O.supercell_coefficients(cell, frag.C), sc.kmesh)
     assert np.abs(eri_k - eri_g).max() < 1e-10 * np.abs(eri_k).max()
+
+
+@pytest.mark.parametrize("kmesh", [(3, 3, 3), (4, 2, 3)])
+def test_time_reversal_half_sum(kmesh):
+    """For real AOs on a Gamma-centred mesh V^{-q} = conj(V^q), and for any
+    orbitals M^{-q}_{(qp),I} = conj(M^q_{(pq),I}) (shift k by q in Eq. 20).
+    Hence E = sum_q M^q V^q M^q^H equals G + swapconj(G) with G over one member
+    of each pair {q, -q} and half of each self-conjugate q: the identity that
+    lets the contraction visit about half of the q-points."""
+    cell = tiny_cell(kmesh=kmesh, shells=[W.Shell(0, 0, (0.6,), (1.0,)), W.Shell(1, 0, (0.9,), (1.0,)),
+                                          W.Shell(0, 1, (1.2,), (1.0,))])
+    r = O.run_isdf(cell, 12, 7, solve_tol=1e-14)
+    nk, nf = cell.nkpts, 3
+    frag = W.make_fragment(cell, 11, 2, nf)
+    M = O.pair_tensor(O.fragment_T(r["X"], frag.C), cell.kmesh)
+    V = r["V"]
+    km = O.k_minus_table(cell.kmesh)[0]
+    sM, sV = np.abs(M).max(), np.abs(V).max()
+    for q in range(nk):
+        Mswap = M[km[q]].reshape(nf, nf, -1).transpose(1, 0, 2).reshape(nf * nf, -1)
+        assert np.abs(Mswap - M[q].conj()).max() < 1e-12 * sM
+        # V^q is computed per q; at full rank its rounding is amplified by cond(Pi^q)
+        assert np.abs(V[km[q]] - V[q].conj()).max() < 1e-6 * sV
+    E = O.fragment_E(M, V, nk)
+    G = np.zeros_like(E)
+    for q in range(nk):
+        if km[q] < q:
+            continue
+        w = 0.5 if km[q] == q else 1.0
+        G += w * (M[q] @ V[q] @ M[q].conj().T) / nk
+    swap = np.arange(nf * nf).reshape(nf, nf).T.ravel()         # (pq) -> (qp)
+    E2 = G + G[np.ix_(swap, swap)].conj()
+    assert np.abs(E2 - E).max() < 1e-10 * np.abs(E).max()
 
 
 def test_eri_symmetries(c1run):
@@ -381,3 +434,35 @@ def test_mutation_fft_sign_caught(monkeypatch):
     bad = O.coulomb_metric(cell, z, [1])[0, 0, 0]
     assert abs(good - cell.volume * 4 * np.pi / (kvec @ kvec)) < 1e-9 * abs(good)
     assert abs(bad - good) > 1e-3 * abs(good)
+
+
+# ------------------------------------------------------ exchange (Eq. 10)
+def _random_density(cell, seed, nocc=2):
+    rng = np.random.default_rng(seed)
+    Cs = rng.standard_normal((cell.nkpts, cell.nao, nocc)) + 1j * rng.standard_normal((cell.nkpts, cell.nao, nocc))
+    return np.einsum("kmi,kni->kmn", Cs, Cs.conj()) / cell.nao
+
+
+def test_exchange_exact_limit(tiny):
+    """At the pair-space rank the ISDF exchange of Eq. 10 equals the grid-exact
+    exchange (pair densities Poisson-solved on the grid)."""
+    cell, phi, ips, nf = tiny
+    P = _random_density(cell, 4)
+    r = O.run_isdf(cell, nf, 7, solve_tol=1e-14, ips=ips, phi=phi)
+    K = O.exchange_matrix(r["X"], r["V"], P, cell.kmesh)
+    Kx = O.fftdf_exchange_matrix(cell, P, phi=phi)
+    assert np.abs(K - Kx).max() < 1e-9 * np.abs(Kx).max()
+    for k in range(cell.nkpts):
+        assert np.allclose(K[k], K[k].conj().T, atol=1e-12 * np.abs(K).max())
+        assert np.linalg.eigvalsh(-K[k]).min() > -1e-10 * np.abs(K).max()   # exchange is negative semidefinite
+
+
+def test_exchange_error_falls_with_points(tiny):
+    cell, phi, ips, nf = tiny
+    P = _random_density(cell, 5)
+    Kx = O.fftdf_exchange_matrix(cell, P, phi=phi)
+    errs = []
+    for n_p in (8, 24, 64):
+        r = O.run_isdf(cell, n_p, 7, solve_tol=1e-14, ips=ips[:n_p], phi=phi)
+        errs.append(np.abs(O.exchange_matrix(r["X"], r["V"], P, cell.kmesh) - Kx).max())
+    assert errs[0] > errs[1] > errs[2]
