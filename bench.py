@@ -35,6 +35,7 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "fragment-ERI build time at Nk=1000 (s), mixed vs FP64 at ≤1e-6 Ha; %roofline"
 SOLVE_TOL = 1e-7
+OUT_SEPARATE_MAX = 48 << 30   # bytes of ERI outputs kept as separate tensors
 
 
 def measured_peaks():
@@ -130,7 +131,18 @@ def run_gpu(args, rank, world, local_rank):
     dt_out = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
     Cs = [torch.from_numpy(f.C).cuda() for f in frags]
     gs = [torch.from_numpy(f.gamma).cuda() for f in frags]
-    outs = [torch.empty((f.norb,) * 4, dtype=dt_out, device="cuda") for f in frags]
+    # ERI outputs: one tensor per fragment when they fit comfortably, else one
+    # buffer of the largest size that every fragment overwrites in turn (the
+    # fragments are done one after the other on the stream)
+    esz = torch.empty((), dtype=dt_out).element_size()
+    out_bytes = sum(f.norb ** 4 for f in frags) * esz
+    if out_bytes <= OUT_SEPARATE_MAX:
+        outs = [torch.empty((f.norb,) * 4, dtype=dt_out, device="cuda") for f in frags]
+        out_mode = "one tensor per fragment"
+    else:
+        shared = torch.empty(max(f.norb for f in frags) ** 4, dtype=dt_out, device="cuda")
+        outs = [shared[: f.norb ** 4].view((f.norb,) * 4) for f in frags]
+        out_mode = f"one reused buffer (all {len(frags)} ERI tensors: {out_bytes / 2**30:.0f} GiB)"
 
     def step(C_list, g_list):
         g.build_points(wl.n_p, wl.seed)
@@ -219,6 +231,7 @@ def run_gpu(args, rank, world, local_rank):
                    "solve_tol": args.solve_tol, "fragments": len(frags),
                    "sum_nf4": int(sum(f.norb ** 4 for f in frags)),
                    "l2": "inputs larger than L2 (Phi, eta, xi, M, B each > 129 MB)",
+                   "eri_out": out_mode,
                    "parallelism": f"replica x{world}"},
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -227,7 +240,7 @@ def run_gpu(args, rank, world, local_rank):
                      "peak_source": peak_name,
                      "algorithmic_flops_per_launch": herk_flops / max(herk_n, 1),
                      "avg_launch_ms": herk_avg_ms, "launches": herk_n,
-                     "traffic": profile_traffic("k_gemm.cu", args.workload)},
+                     "traffic": profile_traffic("k_tc.cu", args.workload)},
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage.items()},
         "clocks": clk,
         "traces_fragment0": {"E_J": float(ej[0]), "E_K": float(ek[0])},

@@ -127,6 +127,17 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out);
  * handle only. */
 int isdf_coulomb_metric(isdf_handle* h, void* V_out);
 
+/* Step S3 by the route of Eqs. 7-8 (zeta never formed): V_eta^q from the grid
+ * FFT of eta^q (Eq. 7, the integral of Eq. 6 with eta in place of zeta), then
+ * the least-squares solution of Pi W Pi = V_eta (Eq. 8) through the same
+ * truncated factor of Pi as isdf_fit_zeta: W^q = conj(Pi^+) V_eta conj(Pi^+)
+ * (the conjugates express Eq. 8 in this library's index placement of Pi).
+ * Produces the same V^q as isdf_coulomb_metric up to rounding, which here is
+ * multiplied by cond(Pi^q) rather than its square root; computed in FP64 in
+ * both precisions.  Replaces isdf_coulomb_metric (either may precede
+ * isdf_fragment_eri).  V_out as for isdf_coulomb_metric. */
+int isdf_coulomb_metric_eta(isdf_handle* h, void* V_out);
+
 /* Step S4 (Eqs. 17-20, Algorithm 2).  For each fragment f with n_orb[f]
  * orbitals phi_p = Nk^{-1/2} sum_k sum_mu C^k_{mu p} phi^k_mu:
  *   C[f]       device complex128 [Nk][N_AO][n_orb[f]]
@@ -136,15 +147,51 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out);
  *              complex64 in MIXED mode; array or entry may be NULL
  *   ej_out[f]  E_J = 1/2 sum gamma_pq gamma_rs (pq|rs)          (host, may be NULL)
  *   ek_out[f]  E_K = -1/4 sum gamma_ps gamma_rq (pq|rs)         (host, may be NULL)
- * The traces are accumulated in FP64. */
+ * The traces are accumulated in FP64.  Fragments are done one after the
+ * other on the handle's stream, so several entries of eri_out may name the
+ * same buffer (each result then overwrites the previous one).
+ * Device memory: the handle keeps its scratch between calls; when an
+ * allocation for a fragment fails, the grid-sized fit arrays (eta, xi) are
+ * freed and the allocation retried (isdf_get of eta or zeta and
+ * isdf_coulomb_metric_eta then need a new isdf_fit_zeta); the fit frees the
+ * fragment scratch in the same way. */
 int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb,
                       const void* const* C, const void* const* gamma,
                       void* const* eri_out, double* ej_out, double* ek_out);
 
+/* k-point exchange matrix from the ISDF integrals (Eq. 10), FP64:
+ *   K^k_{mu nu} = -(1/Nk) sum_{k'} sum_{lam sig} P^{k'}_{lam sig} (mu k, lam k' | sig k', nu k)
+ * computed as K^k = -(1/Nk) X^k^H Gamma^k X^k with
+ *   rho^{k'} = X^{k'} P^{k'} X^{k'}^H  and  Gamma^k_IJ = sum_{k'} V^{k'-k}_JI rho^{k'}_IJ,
+ * the k'-sum done as a convolution over the k-mesh (DFTs).
+ *   P      device complex128 [Nk][N_AO][N_AO]: AO density matrix per k (density
+ *          sum_k Phi^k_lam P^k_{lam sig} conj(Phi^k_sig) / Nk)
+ *   K_out  device complex128 [Nk][N_AO][N_AO]
+ * Needs the Coulomb metric (either route). */
+int isdf_exchange(isdf_handle* h, const void* P, void* K_out);
+
+/* Time-reversal pairing in isdf_fragment_eri (default on).  For a real AO
+ * basis on a Gamma-centred k-mesh, V^{-q} = conj(V^q), and for any orbitals
+ * M^{-q}_{(qp),I} = conj(M^q_{(pq),I}) (shift k by q in the k-sum of the
+ * pair tensor, Eq. 20).  So the term
+ * of -q in (pq|rs) = (1/Nk) sum_q [M^q V^q M^q^H] equals the term of q with
+ * the pair indices swapped and conjugated, and the sum is taken over about
+ * half of the q-points, then completed by that swap.  enable = 0 sums over all
+ * q-points as written.  The results agree to rounding. */
+int isdf_set_time_reversal(isdf_handle* h, int enable);
+
+/* MIXED mode: device bytes that the fragment contraction may use for the fp16
+ * slices of B (Algorithm 2's B^q = M^q L^q for all q).  B is sliced and
+ * contracted in chunks of q-points that fit this limit, each chunk adding to
+ * the same accumulator, so a smaller limit costs only more launches.  Default
+ * 12 GiB; values below one q-point's slices give one q-point per chunk.
+ * Returns ISDF_ERR_ARG for 0. */
+int isdf_set_workspace_limit(isdf_handle* h, uint64_t bytes);
+
 /* Inspection of intermediate results (device outputs, complex128):
  *   what = 0  X   [Nk][N_P][N_AO]
  *   what = 1  Pi  [Nk][N_P][N_P]
- *   what = 2  eta [Nk][N_P][N_g]        (available until isdf_coulomb_metric)
+ *   what = 2  eta [Nk][N_P][N_g]        (from isdf_fit_zeta until freed, see isdf_fragment_eri)
  *   what = 3  zeta [Nk][N_P][N_g]       (computed on request from the fit)
  * out must hold the whole array.  Returns ISDF_ERR_STATE if the step that
  * produces it has not run. */

@@ -24,7 +24,8 @@ STATUS = {0: "ISDF_OK", -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_OOM", -3: "ISDF_ERR_CU
 
 # Every entry point declared in include/isdf.h.
 EXPORTS = ["isdf_create", "isdf_build_points", "isdf_set_points", "isdf_fit_zeta",
-           "isdf_coulomb_metric", "isdf_fragment_eri", "isdf_get", "isdf_sizes",
+           "isdf_coulomb_metric", "isdf_coulomb_metric_eta", "isdf_fragment_eri", "isdf_exchange",
+           "isdf_set_time_reversal", "isdf_set_workspace_limit", "isdf_get", "isdf_sizes",
            "isdf_launch_count", "isdf_timing_enable", "isdf_timing_get", "isdf_eri_traces_noalloc",
            "isdf_last_error", "isdf_destroy"]
 
@@ -61,7 +62,11 @@ def load(path: Optional[str] = None) -> ct.CDLL:
     lib.isdf_set_points.argtypes = [vp, ct.c_int, i32p]
     lib.isdf_fit_zeta.argtypes = [vp, ct.c_double, i32p]
     lib.isdf_coulomb_metric.argtypes = [vp, vp]
+    lib.isdf_coulomb_metric_eta.argtypes = [vp, vp]
     lib.isdf_fragment_eri.argtypes = [vp, ct.c_int, i32p, ct.POINTER(vp), ct.POINTER(vp), ct.POINTER(vp), dp, dp]
+    lib.isdf_exchange.argtypes = [vp, vp, vp]
+    lib.isdf_set_time_reversal.argtypes = [vp, ct.c_int]
+    lib.isdf_set_workspace_limit.argtypes = [vp, ct.c_uint64]
     lib.isdf_get.argtypes = [vp, ct.c_int, vp]
     lib.isdf_sizes.argtypes = [vp, ct.POINTER(ct.c_int64)]
     lib.isdf_launch_count.argtypes = [vp]
@@ -150,6 +155,14 @@ class Isdf:
     def timing(self, enable: bool):
         self._check(self.lib.isdf_timing_enable(self.h, 1 if enable else 0))
 
+    def set_time_reversal(self, enable: bool):
+        """Pair q with -q in the fragment contraction (default on)."""
+        self._check(self.lib.isdf_set_time_reversal(self.h, 1 if enable else 0))
+
+    def set_workspace_limit(self, nbytes: int):
+        """Device bytes for one q-chunk of the fp16 slices of the mixed contraction."""
+        self._check(self.lib.isdf_set_workspace_limit(self.h, ct.c_uint64(int(nbytes))))
+
     def stage_time(self, stage: int):
         """(device ms summed, launches, algorithmic flops summed) of a stage."""
         ms, n, fl = ct.c_double(), ct.c_int64(), ct.c_double()
@@ -176,6 +189,10 @@ class Isdf:
     def coulomb_metric(self, V_out=None):
         self._check(self.lib.isdf_coulomb_metric(self.h, _ptr(V_out)))
 
+    def coulomb_metric_eta(self, V_out=None):
+        """The Coulomb kernel by Eqs. 7-8 (from eta, zeta never formed)."""
+        self._check(self.lib.isdf_coulomb_metric_eta(self.h, _ptr(V_out)))
+
     def fragment_eri(self, C_list: List, gamma_list: Optional[List] = None, eri_out: Optional[List] = None,
                      traces: bool = True):
         n = len(C_list)
@@ -194,6 +211,11 @@ class Isdf:
             self.h, n, norb.ctypes.data_as(ct.POINTER(ct.c_int32)), Cp, gp, ep,
             ej.ctypes.data_as(dp) if traces else None, ek.ctypes.data_as(dp) if traces else None))
         return ej[:n], ek[:n]
+
+    def exchange(self, P, K_out):
+        """k-point exchange matrix K^k (Eq. 10) for the AO density matrices P^k."""
+        self._check(self.lib.isdf_exchange(self.h, _ptr(P), _ptr(K_out)))
+        return K_out
 
     def get(self, what: int, out):
         self._check(self.lib.isdf_get(self.h, int(what), _ptr(out)))

@@ -156,9 +156,27 @@ size_t herk_tc_split_bytes(int64_t n2, int64_t K);
 void herk_tc_tiles(int64_t n2, std::vector<int2>& tiles);
 size_t herk_tc_ws_bytes(int64_t ntiles);
 cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int64_t ldb, double scale,
-                    void* split, const int2* tiles_d, int ntiles, void* ws, int* err, double2* E);
+                    void* split, const int2* tiles_d, int ntiles, void* ws, int* row_exp, int* err, double2* E);
+// The same in steps, for B addressed as (a, k = Q nJ + J) -> B[slot(Q) sQ + a sA + J]
+// with slot(Q) = qmap[Q] (or Q when qmap is NULL) and split into K chunks: row
+// exponents over all K, then each chunk (accumulate = 0 for the first), then the finish.
+cudaError_t herk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                             int64_t n2, int64_t K, int* row_exp);
+cudaError_t herk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                          int64_t n2, int64_t k0, int64_t Kc, const int* row_exp, void* split, const int2* tiles_d,
+                          int ntiles, void* ws, int accumulate, int* err);
+cudaError_t herk_tc_finish(cudaStream_t st, const void* ws, const int2* tiles_d, int ntiles, int64_t n2,
+                           const int* row_exp, double scale, double2* E);
 // eri[p][q][r][s] (complex64) = E[(p q)][(s r)] (complex128) * scale
 cudaError_t eri_permute_zc(cudaStream_t st, const double2* E, int nf, double scale, float2* eri);
+
+// E_ab += conj(E_{s(a)s(b)}), s((pq)) = (qp), in place (n_f^2 x n_f^2 complex128).
+cudaError_t eri_swapconj_sym(cudaStream_t st, double2* E, int nf);
+// out[b] = sw[b] L[b] over nb blocks of `per` elements (FP64 / to complex64).
+cudaError_t scale_blocks(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, double2* out);
+cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, float2* out);
+// out[b][I][J] = a[b][J][I] * c[b][I][J] for nb blocks of n x n.
+cudaError_t hadamard_t(cudaStream_t st, const double2* a, const double2* c, int n, int nb, double2* out);
 
 // Precision conversions.
 cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n);

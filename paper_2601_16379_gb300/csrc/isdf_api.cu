@@ -57,12 +57,16 @@ struct isdf_handle {
   BasisDev bdev{};
   // owned device buffers by name
   std::vector<std::pair<std::string, DevBuf>> bufs;
-  bool has_points = false, has_fit = false, has_xi = false, has_coulomb = false;
+  bool has_points = false, has_fit = false, has_xi = false, has_eta = false, has_coulomb = false;
   std::vector<int32_t> ips;
   std::vector<int32_t> ranks;
   std::string err;
   int64_t launches = 0;
   std::vector<int2> tiles_host;
+  // device bytes for one q-chunk of the fp16 slices of B (mixed contraction)
+  size_t split_budget = (size_t)12 << 30;
+  // pair q with -q in the fragment contraction (time-reversal symmetry)
+  bool q_sym = true;
   // per-stage event timing
   static constexpr int kStages = 6;
   bool timing = false;
@@ -139,6 +143,36 @@ struct isdf_handle {
         b.second.bytes = 0;
       }
   }
+  // Two groups of large buffers never live at once when HBM is short: the
+  // grid-sized fit intermediates (eta, xi and their work) and the per-fragment
+  // scratch.  An allocation in one group that fails frees the other group and
+  // is tried again; freeing the fit group drops eta and xi (a later isdf_get of
+  // them, or isdf_coulomb_metric_eta, then needs a new isdf_fit_zeta).
+  static bool in_frag_group(const std::string& n) { return n.rfind("frag_", 0) == 0 || n.rfind("tc_", 0) == 0; }
+  static bool in_fit_group(const std::string& n) {
+    return n == "eta" || n == "xi" || n == "xi_f" || n == "grid_work";
+  }
+  bool evict_other(const char* name) {
+    const std::string n(name);
+    bool freed = false;
+    const bool frag = in_frag_group(n);
+    for (auto& b : bufs) {
+      const bool other = frag ? in_fit_group(b.first) : in_frag_group(b.first);
+      if (other && b.second.p) {
+        cudaFree(b.second.p);
+        b.second.p = nullptr;
+        b.second.bytes = 0;
+        freed = true;
+      }
+    }
+    if (freed && frag) has_xi = has_eta = false;
+    return freed;
+  }
+  void* ensure_evict(const char* name, size_t bytes) {
+    void* p = ensure(name, bytes);
+    if (!p && evict_other(name)) p = ensure(name, bytes);
+    return p;
+  }
 };
 
 namespace {
@@ -193,7 +227,7 @@ int fail(isdf_handle* h, int code, const char* fmt, ...) {
   } while (0)
 
 #define ENSURE(var, type, name, count)                                                             \
-  type* var = static_cast<type*>(h->ensure(name, sizeof(type) * (size_t)(count)));                 \
+  type* var = static_cast<type*>(h->ensure_evict(name, sizeof(type) * (size_t)(count)));           \
   if (!var) return fail(h, ISDF_ERR_OOM, "device allocation of %s (%zu bytes) failed", name,      \
                         sizeof(type) * (size_t)(count));
 
@@ -215,6 +249,33 @@ double prim_norm(double a, int lx, int ly, int lz) {
 
 // Algorithmic flops of the pair tensor: T = X C, the k->R DFT of T, the pair
 // products and the R->q DFT (direct per-axis DFTs: n_a complex MACs per point and axis).
+// The q-points whose terms enter E = sum_q B^q B^q^H, with sqrt-weights sw[q].
+// With the time-reversal pairing (real AOs on a Gamma-centred mesh give
+// V^{-q} = conj(V^q); M^{-q}_{(qp)} = conj(M^q_{(pq)}) holds for any orbitals),
+// P_{-q} = swapconj(P_q) for P_q = B^q B^q^H, so E = G + swapconj(G) with
+// G = sum_{q in S} w_q P_q over about half the mesh:
+//   S = { m_0 in [0, n_0/2], and m_1 in [0, n_1/2] when m_0 is its own negative },
+//   w_q = 1/2 when both m_0 and m_1 are their own negatives, else 1,
+// which gives every P_q total weight one in G + swapconj(G).  Without the
+// pairing S is the whole mesh with unit weights.
+void q_point_set(const KMesh& km, bool pair, std::vector<int>& qs, std::vector<double>& sw) {
+  const int n0 = km.n[0], n1 = km.n[1], n2 = km.n[2], nk = n0 * n1 * n2;
+  qs.clear();
+  sw.assign(nk, 1.0);
+  for (int q = 0; q < nk; ++q) {
+    if (!pair) {
+      qs.push_back(q);
+      continue;
+    }
+    const int m0 = q / (n1 * n2), m1 = (q / n2) % n1;
+    const bool self0 = (m0 == 0) || (2 * m0 == n0), self1 = (m1 == 0) || (2 * m1 == n1);
+    const bool in = (2 * m0 <= n0) && (!self0 || 2 * m1 <= n1);
+    if (!in) continue;
+    qs.push_back(q);
+    if (self0 && self1) sw[q] = std::sqrt(0.5);
+  }
+}
+
 double frag_m_flops(int nk, int np, int nf, int nao, const KMesh& km) {
   const double per_pt = 8.0 * (km.n[0] + km.n[1] + km.n[2]);
   return 8.0 * nk * (double)np * nf * nao + per_pt * nk * (double)np * nf + 6.0 * nk * (double)nf * nf * np +
@@ -272,11 +333,45 @@ int finish_points(isdf_handle* h) {
   ENSURE(X, double2, "X", (size_t)h->nk * np * h->nao);
   CK(gather_x(h->st, phi, h->nk, h->nao, h->ng, ipsd, np, X));
   h->has_points = true;
-  h->has_fit = h->has_xi = h->has_coulomb = false;
+  h->has_fit = h->has_xi = h->has_eta = h->has_coulomb = false;
   return ISDF_OK;
 }
 
 }  // namespace
+
+// Shared tail of both Coulomb routes: factor V_xi = L_xi L_xi^H, L^q = W^T L_xi
+// (so V^q = L^q L^q^H), optional output of V^q, precision copies for the fragments.
+int coulomb_tail(isdf_handle* h, double2* Vxi, void* V_out) {
+  const int nk = h->nk, np = h->np;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  double2* W = (double2*)h->buf("W");
+  // V_xi = L_xi L_xi^H ; L^q = W^T L_xi
+  ENSURE(LtV, double2, "LtV", (size_t)nk * np * np);
+  ENSURE(permV, int32_t, "permV", (size_t)nk * np);
+  ENSURE(rankV, int32_t, "rankV", nk);
+  ENSURE(dwork, double, "chol_dwork", (size_t)nk * 2 * np);
+  CK(pchol_batched(h->st, Vxi, np, nk, 1e-15, LtV, permV, rankV, dwork));
+  ENSURE(Lxi, double2, "W_work", (size_t)nk * np * np);
+  CK(lt_to_rowmajor(h->st, LtV, rankV, np, nk, Lxi));
+  ENSURE(Lq, double2, "Lq", (size_t)nk * np * np);
+  CK(zgemm(h->st, 'T', 'N', np, np, np, one, W, np, (int64_t)np * np, Lxi, np, (int64_t)np * np, zero, Lq, np,
+           (int64_t)np * np, nk));
+  if (V_out) {
+    // V^q = W^T V_xi conj(W)
+    double2* tmp = Lxi;  // reuse
+    CK(zgemm(h->st, 'N', 'R', np, np, np, one, Vxi, np, (int64_t)np * np, W, np, (int64_t)np * np, zero, tmp, np,
+             (int64_t)np * np, nk));
+    CK(zgemm(h->st, 'T', 'N', np, np, np, one, W, np, (int64_t)np * np, tmp, np, (int64_t)np * np, zero,
+             (double2*)V_out, np, (int64_t)np * np, nk));
+  }
+  if (h->prec == ISDF_MIXED) {
+    ENSURE(Xf, float2, "X_f", (size_t)nk * np * h->nao);
+    CK(z2c(h->st, (const double2*)h->buf("X"), Xf, (int64_t)nk * np * h->nao));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  h->has_coulomb = true;
+  return ISDF_OK;
+}
 
 extern "C" {
 
@@ -503,6 +598,7 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
     if (h->ranks[q] < 1) return fail(h, ISDF_ERR_NUMERIC, "Pi^q has rank 0 at q=%d", q);
   h->has_fit = true;
   h->has_xi = true;
+  h->has_eta = true;
   h->has_coulomb = false;
   return ISDF_OK;
 }
@@ -537,34 +633,43 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
     CK(c2z(h->st, Vxif, Vxi, (int64_t)nk * np * np));
   }
   h->has_xi = false;  // xi was transformed in place (FP64) / is no longer needed
-  // V_xi = L_xi L_xi^H ; L^q = W^T L_xi
-  ENSURE(LtV, double2, "LtV", (size_t)nk * np * np);
-  ENSURE(permV, int32_t, "permV", (size_t)nk * np);
-  ENSURE(rankV, int32_t, "rankV", nk);
-  ENSURE(dwork, double, "chol_dwork", (size_t)nk * 2 * np);
-  CK(pchol_batched(h->st, Vxi, np, nk, 1e-15, LtV, permV, rankV, dwork));
-  ENSURE(Lxi, double2, "W_work", (size_t)nk * np * np);
-  CK(lt_to_rowmajor(h->st, LtV, rankV, np, nk, Lxi));
-  ENSURE(Lq, double2, "Lq", (size_t)nk * np * np);
-  CK(zgemm(h->st, 'T', 'N', np, np, np, one, W, np, (int64_t)np * np, Lxi, np, (int64_t)np * np, zero, Lq, np,
+  return coulomb_tail(h, Vxi, V_out);
+}
+
+// Coulomb kernel without forming zeta (Eqs. 7-8): V_eta = Omega c'^* c'^T from
+// the grid FFT of eta (Eq. 7), then V_xi = conj(W) V_eta W^T, which is
+// W^T V_xi conj(W) = conj(Pi^+) V_eta conj(Pi^+) for the kernel of zeta
+// (the least-squares solution of Eq. 8).  Always FP64: rounding in V_eta is
+// multiplied by cond(Pi) on the way to W.
+int isdf_coulomb_metric_eta(isdf_handle* h, void* V_out) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!h->has_fit || !h->has_eta)
+    return fail(h, ISDF_ERR_STATE, "isdf_coulomb_metric_eta needs eta from isdf_fit_zeta (released after fragments)");
+  const int nk = h->nk, np = h->np, ng = h->ng;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  double2* eta = (double2*)h->buf("eta");
+  double2* W = (double2*)h->buf("W");
+  double2* work = (double2*)h->buf("xi");  // the copy of eta is transformed in place
+  const double2* tw = (const double2*)h->buf("grid_tw");
+  StageTimer stt(h, 2, 4.0 * nk * (double)np * np * ng);
+  ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
+  ENSURE(Veta, double2, "Veta", (size_t)nk * np * np);
+  ENSURE(gwork, uint8_t, "grid_work", grid_coulomb_work_bytes(nk, h->cell));
+  CK(cudaMemcpyAsync(work, eta, sizeof(double2) * (size_t)nk * np * ng, cudaMemcpyDeviceToDevice, h->st));
+  h->has_xi = false;
+  CK(grid_coulomb_fft(h->st, work, np, 0, nk, h->cell, tw, gwork));
+  CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), work, ng, (int64_t)np * ng, work, ng,
+           (int64_t)np * ng, zero, Veta, np, (int64_t)np * np, nk));
+  // V_xi = conj(W) (V_eta W^T)
+  double2* tmp = (double2*)h->ensure("W_work", sizeof(double2) * (size_t)nk * np * np);
+  if (!tmp) return fail(h, ISDF_ERR_OOM, "workspace");
+  CK(zgemm(h->st, 'N', 'T', np, np, np, one, Veta, np, (int64_t)np * np, W, np, (int64_t)np * np, zero, tmp, np,
            (int64_t)np * np, nk));
-  if (V_out) {
-    // V^q = W^T V_xi conj(W)
-    double2* tmp = Lxi;  // reuse
-    CK(zgemm(h->st, 'N', 'R', np, np, np, one, Vxi, np, (int64_t)np * np, W, np, (int64_t)np * np, zero, tmp, np,
-             (int64_t)np * np, nk));
-    CK(zgemm(h->st, 'T', 'N', np, np, np, one, W, np, (int64_t)np * np, tmp, np, (int64_t)np * np, zero,
-             (double2*)V_out, np, (int64_t)np * np, nk));
-  }
-  if (h->prec == ISDF_MIXED) {
-    ENSURE(Lqf, float2, "Lq_f", (size_t)nk * np * np);
-    CK(z2c(h->st, Lq, Lqf, (int64_t)nk * np * np));
-    ENSURE(Xf, float2, "X_f", (size_t)nk * np * h->nao);
-    CK(z2c(h->st, (const double2*)h->buf("X"), Xf, (int64_t)nk * np * h->nao));
-  }
-  CK(cudaStreamSynchronize(h->st));
-  h->has_coulomb = true;
-  return ISDF_OK;
+  CK(zgemm(h->st, 'R', 'N', np, np, np, one, W, np, (int64_t)np * np, tmp, np, (int64_t)np * np, zero, Vxi, np,
+           (int64_t)np * np, nk));
+  return coulomb_tail(h, Vxi, V_out);
 }
 
 int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const void* const* C,
@@ -582,9 +687,31 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     if (nf < 1 || nf > 4096 || !C[f]) return fail(h, ISDF_ERR_ARG, "fragment %d: bad size or NULL C", f);
     if ((int64_t)nf * nf > 65535LL * 64) return fail(h, ISDF_ERR_ARG, "fragment %d too large", f);
   }
+  if (n_frag == 0) return ISDF_OK;
+  // The q-points whose B^q enter E, their weights folded into L^q, and their runs.
+  std::vector<int> qs;
+  std::vector<double> sw;
+  q_point_set(km, h->q_sym, qs, sw);
+  const int nS = (int)qs.size();
+  std::vector<std::pair<int, int>> runs;  // (first q, count) of consecutive q-points
+  for (int j = 0; j < nS; ++j) {
+    if (!runs.empty() && runs.back().first + runs.back().second == qs[j])
+      ++runs.back().second;
+    else
+      runs.push_back({qs[j], 1});
+  }
+  std::vector<int> slot(nk, -1);  // position of q in the compact order
+  for (int j = 0; j < nS; ++j) slot[qs[j]] = j;
+  ENSURE(qmap, int, "frag_qmap", nS);
+  ENSURE(swd, double, "frag_sw", nk);
+  CK(cudaMemcpyAsync(qmap, qs.data(), sizeof(int) * nS, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(swd, sw.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, h->st));
+  const double2* Lq = (const double2*)h->buf("Lq");
+  const int64_t pp = (int64_t)np * np;
   for (int f = 0; f < n_frag; ++f) {
     const int nf = n_orb[f];
     const int64_t n2 = (int64_t)nf * nf;
+    const int64_t sq = n2 * np;  // q stride of M
     const double2* Cf = (const double2*)C[f];
     double* trf = nullptr;
     const bool want_tr = (ej_out || ek_out) && gamma && gamma[f];
@@ -595,11 +722,12 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     if (!mixed) {
       const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
       double2* X = (double2*)h->buf("X");
-      double2* Lq = (double2*)h->buf("Lq");
+      ENSURE(Lw, double2, "frag_Lw", (size_t)nk * pp);
       ENSURE(T, double2, "frag_T", (size_t)nk * np * nf);
-      ENSURE(M, double2, "frag_M", (size_t)nk * n2 * np);
-      ENSURE(B, double2, "frag_B", (size_t)n2 * nk * np);
+      ENSURE(M, double2, "frag_M", (size_t)nk * sq);
+      ENSURE(B, double2, "frag_B", (size_t)n2 * nS * np);
       ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
+      if (f == 0) CK(scale_blocks(h->st, Lq, pp, nk, swd, Lw));
       {
         StageTimer stt(h, 3, frag_m_flops(nk, np, nf, nao, km));
         CK(zgemm(h->st, 'N', 'N', np, nf, nao, one, X, nao, (int64_t)np * nao, Cf, nf, (int64_t)nao * nf, zero, T,
@@ -609,36 +737,43 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         CK(kdft_cols(h->st, M, n2 * np, km, +1, +1, 0, 1.0 / nk));
       }
       {
-        StageTimer stt(h, 4, 8.0 * (double)n2 * np * np * nk);
-        CK(zgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lq, np, (int64_t)np * np, zero, B,
-                 (int64_t)nk * np, np, nk));
+        // B = [w_q^{1/2} M^q L^q]_{q in S}, compact: B[a][slot(q) np + J]
+        StageTimer stt(h, 4, 8.0 * (double)n2 * pp * nS);
+        for (const auto& r : runs)
+          CK(zgemm(h->st, 'N', 'N', (int)n2, np, np, one, M + r.first * sq, np, sq, Lw + r.first * pp, np, pp, zero,
+                   B + (int64_t)slot[r.first] * np, (int64_t)nS * np, np, r.second));
       }
       {
-        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nk * np);
-        CK(zgemm(h->st, 'N', 'C', (int)n2, (int)n2, nk * np, one, B, (int64_t)nk * np, 0, B, (int64_t)nk * np, 0,
+        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nS * np);
+        CK(zgemm(h->st, 'N', 'C', (int)n2, (int)n2, nS * np, one, B, (int64_t)nS * np, 0, B, (int64_t)nS * np, 0,
                  zero, E, n2, 0, 1));
+        if (h->q_sym) CK(eri_swapconj_sym(h->st, E, nf));
       }
       if (eri_out && eri_out[f]) CK(eri_permute(h->st, E, nf, 1.0 / nk, (double2*)eri_out[f]));
       if (want_tr) CK(eri_traces(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf));
     } else {
       const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
       float2* Xf = (float2*)h->buf("X_f");
-      float2* Lqf = (float2*)h->buf("Lq_f");
+      ENSURE(Lwf, float2, "frag_Lwf", (size_t)nk * pp);
       ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nf);
       ENSURE(T, float2, "frag_Tf", (size_t)nk * np * nf);
-      ENSURE(M, float2, "frag_Mf", (size_t)nk * n2 * np);
-      ENSURE(B, float2, "frag_Bf", (size_t)n2 * nk * np);
+      ENSURE(M, float2, "frag_Mf", (size_t)nk * sq);
       ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
       std::vector<int2>& tl = h->tiles_host;
       herk_tc_tiles(n2, tl);
-      const int64_t Kq = (int64_t)nk * np;
-      ENSURE(split, uint8_t, "tc_split", herk_tc_split_bytes(n2, Kq));
+      // B^q = w_q^{1/2} M^q L^q overwrites M^q, qc q-points at a time through Bc; the
+      // contraction then takes the B^q of S in chunks of qc q-points (fp16 slices of qc np columns).
+      const size_t per_q = herk_tc_split_bytes(n2, np);
+      const int qc = (int)std::max<int64_t>(1, std::min<int64_t>(nS, (int64_t)(h->split_budget / per_q)));
+      ENSURE(split, uint8_t, "tc_split", herk_tc_split_bytes(n2, (int64_t)qc * np));
+      ENSURE(Bc, float2, "frag_Bc", (size_t)qc * sq);
+      ENSURE(rexp, int, "tc_rowexp", n2);
       ENSURE(tiles_d, int2, "tc_tiles", tl.size());
       ENSURE(ws, uint8_t, "tc_ws", herk_tc_ws_bytes((int64_t)tl.size()));
       ENSURE(tcw, int, "tc_words", 4);
       CK(cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
       CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
-
+      if (f == 0) CK(scale_blocks_f(h->st, Lq, pp, nk, swd, Lwf));
       {
         StageTimer stt(h, 3, frag_m_flops(nk, np, nf, nao, km));
         CK(z2c(h->st, Cf, Cff, (int64_t)nk * nao * nf));
@@ -649,13 +784,25 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         CK(kdft_cols_f(h->st, M, n2 * np, km, +1, +1, 0, 1.f / nk));
       }
       {
-        StageTimer stt(h, 4, 8.0 * (double)n2 * np * np * nk);
-        CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M, np, n2 * np, Lqf, np, (int64_t)np * np, zero, B,
-                 (int64_t)nk * np, np, nk));
+        StageTimer stt(h, 4, 8.0 * (double)n2 * pp * nS);
+        for (const auto& r : runs)
+          for (int q0 = r.first; q0 < r.first + r.second; q0 += qc) {
+            const int nq = std::min(qc, r.first + r.second - q0);
+            CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M + q0 * sq, np, sq, Lwf + q0 * pp, np, pp, zero, Bc,
+                     np, sq, nq));
+            CK(cudaMemcpyAsync(M + q0 * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice, h->st));
+          }
       }
       {
-        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nk * np);
-        CK(herk_tc(h->st, B, n2, Kq, Kq, 1.0 / nk, split, tiles_d, (int)tl.size(), ws, tcw + 1, E));
+        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nS * np);
+        CK(herk_tc_rowscale(h->st, M, sq, np, np, qmap, n2, (int64_t)nS * np, rexp));
+        for (int j0 = 0; j0 < nS; j0 += qc) {
+          const int nq = std::min(qc, nS - j0);
+          CK(herk_tc_chunk(h->st, M, sq, np, np, qmap, n2, (int64_t)j0 * np, (int64_t)nq * np, rexp, split, tiles_d,
+                           (int)tl.size(), ws, j0 > 0, tcw + 1));
+        }
+        CK(herk_tc_finish(h->st, ws, tiles_d, (int)tl.size(), n2, rexp, 1.0 / nk, E));
+        if (h->q_sym) CK(eri_swapconj_sym(h->st, E, nf));
       }
       if (eri_out && eri_out[f]) CK(eri_permute_zc(h->st, E, nf, 1.0, (float2*)eri_out[f]));
       if (want_tr) CK(eri_traces(h->st, E, nf, 1.0, (const double2*)gamma[f], trf));
@@ -680,6 +827,54 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
   return ISDF_OK;
 }
 
+int isdf_exchange(isdf_handle* h, const void* P, void* K_out) {
+  if (!h || !P || !K_out) return fail(h, ISDF_ERR_ARG, "isdf_exchange: NULL argument");
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!h->has_coulomb) return fail(h, ISDF_ERR_STATE, "isdf_exchange before the Coulomb metric");
+  const int nk = h->nk, np = h->np, nao = h->nao;
+  const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  double2* X = (double2*)h->buf("X");
+  double2* Lq = (double2*)h->buf("Lq");
+  ENSURE(rho, double2, "kx_rho", (size_t)nk * np * np);
+  ENSURE(Vd, double2, "kx_V", (size_t)nk * np * np);
+  ENSURE(t1, double2, "kx_t1", (size_t)nk * np * (nao > np ? nao : np));
+  // rho^k = X^k P^k X^k^H
+  CK(zgemm(h->st, 'N', 'N', np, nao, nao, one, X, nao, (int64_t)np * nao, (const double2*)P, nao,
+           (int64_t)nao * nao, zero, t1, nao, (int64_t)np * nao, nk));
+  CK(zgemm(h->st, 'N', 'C', np, np, nao, one, t1, nao, (int64_t)np * nao, X, nao, (int64_t)np * nao, zero, rho, np,
+           (int64_t)np * np, nk));
+  // V^q = L^q L^q^H
+  CK(zgemm(h->st, 'N', 'C', np, np, np, one, Lq, np, (int64_t)np * np, Lq, np, (int64_t)np * np, zero, Vd, np,
+           (int64_t)np * np, nk));
+  // Gamma^k = sum_k' (V^{k'-k})^T o rho^{k'}: DFT_- V, DFT_+ rho, transposed product, DFT_- / Nk
+  CK(kdft_cols(h->st, Vd, (int64_t)np * np, km, -1, -1, 0, 1.0));
+  CK(kdft_cols(h->st, rho, (int64_t)np * np, km, +1, +1, 0, 1.0));
+  CK(hadamard_t(h->st, Vd, rho, np, nk, rho));
+  CK(kdft_cols(h->st, rho, (int64_t)np * np, km, -1, -1, 0, 1.0 / nk));
+  // K^k = -(1/Nk) X^k^H Gamma^k X^k
+  CK(zgemm(h->st, 'N', 'N', np, nao, np, one, rho, np, (int64_t)np * np, X, nao, (int64_t)np * nao, zero, t1, nao,
+           (int64_t)np * nao, nk));
+  CK(zgemm(h->st, 'C', 'N', nao, nao, np, make_double2(-1.0 / nk, 0.0), X, nao, (int64_t)np * nao, t1, nao,
+           (int64_t)np * nao, zero, (double2*)K_out, nao, (int64_t)nao * nao, nk));
+  CK(cudaStreamSynchronize(h->st));
+  return ISDF_OK;
+}
+
+int isdf_set_time_reversal(isdf_handle* h, int enable) {
+  if (!h) return ISDF_ERR_ARG;
+  h->q_sym = (enable != 0);
+  return ISDF_OK;
+}
+
+int isdf_set_workspace_limit(isdf_handle* h, uint64_t bytes) {
+  if (!h) return ISDF_ERR_ARG;
+  if (bytes == 0) return fail(h, ISDF_ERR_ARG, "workspace limit must be positive");
+  h->split_budget = (size_t)bytes;
+  return ISDF_OK;
+}
+
 int isdf_get(isdf_handle* h, int what, void* out) {
   if (!h || !out) return ISDF_ERR_ARG;
   LaunchScope ls(h);
@@ -695,7 +890,7 @@ int isdf_get(isdf_handle* h, int what, void* out) {
       CK(cudaMemcpyAsync(out, h->buf("Pi"), sizeof(double2) * (size_t)nk * np * np, cudaMemcpyDeviceToDevice, h->st));
       break;
     case 2:
-      if (!h->has_fit) return fail(h, ISDF_ERR_STATE, "eta not available");
+      if (!h->has_eta) return fail(h, ISDF_ERR_STATE, "eta not available (needs isdf_fit_zeta)");
       CK(cudaMemcpyAsync(out, h->buf("eta"), sizeof(double2) * (size_t)nk * np * ng, cudaMemcpyDeviceToDevice, h->st));
       break;
     case 3: {

@@ -99,6 +99,52 @@ __global__ void __launch_bounds__(256) traces_final_kernel(const double2* __rest
   }
 }
 
+// out[b][I][J] = a[b][J][I] * c[b][I][J]  (n x n blocks)
+__global__ void hadamard_t_kernel(const double2* __restrict__ a, const double2* __restrict__ c, int n, int nb,
+                                  double2* __restrict__ out) {
+  const int64_t per = (int64_t)n * n, total = per * nb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / per;
+    const int I = (int)((e % per) / n), J = (int)(e % n);
+    out[e] = cmul(a[b * per + (int64_t)J * n + I], c[e]);
+  }
+}
+
+// E_ab <- E_ab + conj(E_{s(a) s(b)}) with s((p q)) = (q p).  Each orbit {e, e'}
+// of the involution is handled by the thread of its smaller index, so the
+// update is in place without races.
+__global__ void swapconj_sym_kernel(double2* __restrict__ E, int nf) {
+  const int64_t n2 = (int64_t)nf * nf, total = n2 * n2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / n2, b = e % n2;
+    const int64_t sa = (a % nf) * nf + a / nf, sb = (b % nf) * nf + b / nf;
+    const int64_t e2 = sa * n2 + sb;
+    if (e2 < e) continue;
+    const double2 x = E[e];
+    if (e2 == e) {
+      E[e] = make_double2(2.0 * x.x, 0.0);
+    } else {
+      const double2 y = E[e2];
+      E[e] = make_double2(x.x + y.x, x.y - y.y);
+      E[e2] = make_double2(y.x + x.x, y.y - x.y);
+    }
+  }
+}
+
+// out[b] = sw[b] * L[b] for blocks of `per` elements, converted to TO.
+template <typename TO>
+__global__ void scale_blocks_kernel(const double2* __restrict__ L, int64_t per, int nb, const double* __restrict__ sw,
+                                    TO* __restrict__ out) {
+  const int64_t total = per * nb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const double w = sw[e / per];
+    TO o;
+    o.x = L[e].x * w;
+    o.y = L[e].y * w;
+    out[e] = o;
+  }
+}
+
 __global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = make_float2((float)in[e].x, (float)in[e].y);
@@ -158,6 +204,28 @@ cudaError_t eri_traces_f(cudaStream_t st, const float2* E, int nf, double scale,
                          double* out) {
   double2* part = reinterpret_cast<double2*>(out + 4);
   return traces_impl<float2>(st, E, nf, scale, gamma, out, part);
+}
+
+cudaError_t eri_swapconj_sym(cudaStream_t st, double2* E, int nf) {
+  swapconj_sym_kernel<<<nblocks((int64_t)nf * nf * nf * nf), 256, 0, st>>>(E, nf);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t scale_blocks(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, double2* out) {
+  scale_blocks_kernel<double2><<<nblocks(per * nb), 256, 0, st>>>(L, per, nb, sw, out);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, float2* out) {
+  scale_blocks_kernel<float2><<<nblocks(per * nb), 256, 0, st>>>(L, per, nb, sw, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t hadamard_t(cudaStream_t st, const double2* a, const double2* c, int n, int nb, double2* out) {
+  hadamard_t_kernel<<<nblocks((int64_t)n * n * nb), 256, 0, st>>>(a, c, n, nb, out);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n) {

@@ -33,6 +33,8 @@
 #include <cstring>
 #include <vector>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace isdf {
@@ -147,6 +149,7 @@ struct TileArgs {
   float* ws_hi;        // [tile][BN][BM] float-float sums, high part
   float* ws_lo;        // low part
   int nkb;             // k-blocks of BK
+  int accumulate;      // 1: add to the workspace of an earlier launch (K chunks)
   int* err;            // device error word
 };
 
@@ -277,7 +280,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint32_t v0[32];
         float H[32], L[32];
         const size_t base = (size_t)(cb * 32) * BM + row;
-        if (c > 0) {
+        const bool fresh = (c == 0) && !args.accumulate;
+        if (!fresh) {
           // issue all 64 global loads of this column block before the TMEM reads
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float a0 = __uint_as_float(v0[j]);
-          if (c == 0) {
+          if (fresh) {
             H[j] = a0;
             L[j] = 0.f;
           } else {
@@ -335,14 +339,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ----------------------------------------------------------------- helpers
+// B is addressed as element (a, k), k = Q nJ + J, at B[slot(Q) sQ + a sA + J]
+// (J < nJ), slot(Q) = qmap[Q], or Q without a map.
+struct BView {
+  const float2* p;
+  int64_t sQ, sA, nJ;
+  const int* qmap;
+  __device__ __forceinline__ float2 at(int64_t a, int64_t k) const {
+    const int64_t Q = k / nJ, J = k - Q * nJ;
+    const int64_t slot = qmap ? (int64_t)__ldg(qmap + Q) : Q;
+    return p[slot * sQ + a * sA + J];
+  }
+};
+
 // Per complex row a: exponent e_a with max_k max(|Re B_ak|, |Im B_ak|) 2^e_a in [64, 128).
-__global__ void row_scale_kernel(const float2* __restrict__ B, int64_t n2, int64_t K, int64_t ld,
-                                 int* __restrict__ row_exp) {
+__global__ void row_scale_kernel(BView B, int64_t n2, int64_t K, int* __restrict__ row_exp) {
   const int64_t a = blockIdx.x;
   if (a >= n2) return;
   float m = 0.f;
   for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-    const float2 v = B[a * ld + k];
+    const float2 v = B.at(a, k);
     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
   __shared__ float sm[32];
@@ -358,14 +374,14 @@ __global__ void row_scale_kernel(const float2* __restrict__ B, int64_t n2, int64
 
 // Slices of A': row 2a = P_a (Re, Im interleaved), row 2a+1 = Q_a (Im, -Re); columns
 // beyond 2K are zero.  v = x 2^e_a = s1 + s2/128 + s3/128^2 (+ remainder).
-__global__ void split_kernel(const float2* __restrict__ B, int64_t n2, int64_t K, int64_t ld, int64_t K2,
+__global__ void split_kernel(BView B, int64_t n2, int64_t k0, int64_t K, int64_t K2,
                              const int* __restrict__ row_exp, __half* __restrict__ S1, __half* __restrict__ S2,
                              __half* __restrict__ S3) {
   const int64_t total = n2 * (K2 / 2);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = e / (K2 / 2), k = e % (K2 / 2);
     float2 v = make_float2(0.f, 0.f);
-    if (k < K) v = B[a * ld + k];
+    if (k < K) v = B.at(a, k0 + k);
     const int ex = row_exp[a];
     const float pr = ldexpf(v.x, ex), pi = ldexpf(v.y, ex);
     const float vals[4] = {pr, pi, pi, -pr};
@@ -455,34 +471,47 @@ inline int nblk(int64_t total) {
 
 size_t herk_tc_split_bytes(int64_t n2, int64_t K) {
   const int64_t K2 = ((2 * K + tc::BK - 1) / tc::BK) * tc::BK;
-  return (size_t)tc::NSLICE * (2 * n2) * K2 * sizeof(__half) + (size_t)n2 * sizeof(int) + 256;
+  return (size_t)tc::NSLICE * (2 * n2) * K2 * sizeof(__half) + 256;
 }
 
+// Lower-triangle tiles in launch order.  Every CTA streams the whole K extent of
+// its A' and B' rows, and about one CTA per SM is resident, so the order decides
+// what L2 can share: tiles go in bands of kGroupA A'-tiles, and within a band
+// column by column, so that the ~150 CTAs of a wave read about 12 A'-blocks and
+// 12 B'-blocks instead of ~150 different A'-blocks.
 void herk_tc_tiles(int64_t n2, std::vector<int2>& tiles) {
+  constexpr int64_t kGroupA = 12;
   tiles.clear();
   const int64_t mt = (2 * n2 + tc::BM - 1) / tc::BM, nt = (n2 + tc::BN - 1) / tc::BN;
-  for (int64_t tj = 0; tj < nt; ++tj)
-    for (int64_t ti = 0; ti < mt; ++ti)
-      if (ti * (tc::BM / 2) + (tc::BM / 2 - 1) >= tj * tc::BN) tiles.push_back(make_int2((int)ti, (int)tj));
+  for (int64_t t0 = 0; t0 < mt; t0 += kGroupA)
+    for (int64_t tj = 0; tj < nt; ++tj)
+      for (int64_t ti = t0; ti < std::min(mt, t0 + kGroupA); ++ti)
+        if (ti * (tc::BM / 2) + (tc::BM / 2 - 1) >= tj * tc::BN) tiles.push_back(make_int2((int)ti, (int)tj));
 }
 
 size_t herk_tc_ws_bytes(int64_t ntiles) { return (size_t)ntiles * tc::BN * tc::BM * 2 * sizeof(float); }
 
-// E (complex128 n2 x n2) = scale * B B^H, B complex64 n2 x K (row pitch ldb).
-// split: device buffer of herk_tc_split_bytes; tiles_d: device copy of herk_tc_tiles;
-// ws: herk_tc_ws_bytes; err: 1 device int (0 on entry).
-cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int64_t ldb, double scale,
-                    void* split, const int2* tiles_d, int ntiles, void* ws, int* err, double2* E) {
+// Row exponents over the whole row: element (a, k) = B[slot(Q) sQ + a sA + J], k = Q nJ + J < K.
+cudaError_t herk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                             int64_t n2, int64_t K, int* row_exp) {
+  tc::BView bv{B, sQ, sA, nJ, qmap};
+  tc::row_scale_kernel<<<(unsigned)n2, 256, 0, st>>>(bv, n2, K, row_exp);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ws (+)= slices of columns [k0, k0 + Kc) of B: one K chunk of E = B B^H.
+cudaError_t herk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                          int64_t n2, int64_t k0, int64_t Kc, const int* row_exp, void* split, const int2* tiles_d,
+                          int ntiles, void* ws, int accumulate, int* err) {
   using namespace tc;
-  if (n2 <= 0 || K <= 0 || ntiles <= 0) return cudaSuccess;
-  const int64_t K2 = ((2 * K + BK - 1) / BK) * BK;
+  if (n2 <= 0 || Kc <= 0 || ntiles <= 0) return cudaSuccess;
+  const int64_t K2 = ((2 * Kc + BK - 1) / BK) * BK;
   __half* S1 = reinterpret_cast<__half*>(split);
   __half* S2 = S1 + (size_t)(2 * n2) * K2;
   __half* S3 = S2 + (size_t)(2 * n2) * K2;
-  int* row_exp = reinterpret_cast<int*>(S3 + (size_t)(2 * n2) * K2);
-  row_scale_kernel<<<(unsigned)n2, 256, 0, st>>>(B, n2, K, ldb, row_exp);
-  count_launch();
-  split_kernel<<<nblk(n2 * (K2 / 2)), 256, 0, st>>>(B, n2, K, ldb, K2, row_exp, S1, S2, S3);
+  BView bv{B, sQ, sA, nJ, qmap};
+  split_kernel<<<nblk(n2 * (K2 / 2)), 256, 0, st>>>(bv, n2, k0, Kc, K2, row_exp, S1, S2, S3);
   count_launch();
   CUtensorMap mA[3], mB[3];
   __half* sl[3] = {S1, S2, S3};
@@ -494,15 +523,32 @@ cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int
   if (e != cudaSuccess) return e;
   float* wh = reinterpret_cast<float*>(ws);
   float* wl = wh + (size_t)ntiles * BN * BM;
-  TileArgs args{tiles_d, wh, wl, (int)(K2 / BK), err};
+  TileArgs args{tiles_d, wh, wl, (int)(K2 / BK), accumulate, err};
   herk_tc_kernel<<<ntiles, NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], args);
   count_launch();
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// E (complex128 n2 x n2, full Hermitian) = scale * 2^-(e_a + e_b) * workspace.
+cudaError_t herk_tc_finish(cudaStream_t st, const void* ws, const int2* tiles_d, int ntiles, int64_t n2,
+                           const int* row_exp, double scale, double2* E) {
+  using namespace tc;
+  const float* wh = reinterpret_cast<const float*>(ws);
+  const float* wl = wh + (size_t)ntiles * BN * BM;
   herk_finish_kernel<<<nblk((int64_t)ntiles * BN * (BM / 2)), 256, 0, st>>>(wh, wl, tiles_d, ntiles, n2, row_exp,
                                                                             scale, E);
   count_launch();
   return cudaGetLastError();
+}
+
+// One-shot E = scale * B B^H for B complex64 n2 x K with row pitch ldb.
+cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int64_t ldb, double scale,
+                    void* split, const int2* tiles_d, int ntiles, void* ws, int* row_exp, int* err, double2* E) {
+  cudaError_t e = herk_tc_rowscale(st, B, 0, ldb, K, nullptr, n2, K, row_exp);
+  if (e != cudaSuccess) return e;
+  e = herk_tc_chunk(st, B, 0, ldb, K, nullptr, n2, 0, K, row_exp, split, tiles_d, ntiles, ws, 0, err);
+  if (e != cudaSuccess) return e;
+  return herk_tc_finish(st, ws, tiles_d, ntiles, n2, row_exp, scale, E);
 }
 
 }  // namespace isdf

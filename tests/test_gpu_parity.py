@@ -194,6 +194,68 @@ def test_mixed_eri_c1(cuda, lib_built, c1):
         assert abs(ej[i] - rj) < MIXED_TOL and abs(ek[i] - rk) < MIXED_TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_time_reversal_pairing_matches_full_sum(cuda, lib_built, c2, prec):
+    """The contraction over about half of the q-points completed by the
+    (pq) -> (qp) conjugate swap (15 of the 27 q-points on the 3x3x3 mesh) gives
+    the ERIs and traces of the sum over all q, and both match the oracle."""
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c2
+    tol = 1e-7
+    res = {}
+    for pair in (True, False):
+        g = B.Isdf(wl.cell, prec)
+        g.set_time_reversal(pair)
+        g.build_points(wl.n_p, wl.seed)
+        g.fit_zeta(tol)
+        g.coulomb_metric()
+        res[pair] = gpu_eri(cuda, g, wl.fragments, prec)
+        g.close()
+    bound = FP64_TOL if prec == 0 else MIXED_TOL
+    for i, f in enumerate(wl.fragments):
+        ref, (rj, rk) = o.eri(tol, f)
+        for pair in (True, False):
+            eris, ej, ek = res[pair]
+            assert np.abs(eris[i] - ref).max() < bound
+            assert abs(ej[i] - rj) < bound and abs(ek[i] - rk) < bound
+        assert np.abs(res[True][0][i] - res[False][0][i]).max() < bound
+        assert abs(res[True][1][i] - res[False][1][i]) < bound
+
+
+@pytest.mark.parametrize("qc", [1, 4])
+def test_mixed_q_chunks_c2(cuda, lib_built, c2, qc):
+    """The mixed contraction taken in q-chunks (qc q-points of B per launch; the
+    15 paired q-points of the 3x3x3 mesh give a ragged last chunk for qc = 4)
+    accumulates the same E as one launch over all of them, and stays within the
+    mixed tolerance of the oracle."""
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c2
+    tol = 1e-7
+    f = wl.fragments[0]
+    n2, np_ = f.norb ** 2, wl.n_p
+    k2 = -(-2 * np_ // 64) * 64                 # fp16 columns of one q-point, padded to 64
+    per_q = 3 * (2 * n2) * k2 * 2 + 256           # three slices of the 2 n2 real rows
+    res = {}
+    for limit in (None, qc * per_q):
+        g = B.Isdf(wl.cell, B.ISDF_MIXED)
+        if limit is not None:
+            g.set_workspace_limit(1 if qc == 1 else limit)
+        g.build_points(wl.n_p, wl.seed)
+        g.fit_zeta(tol)
+        g.coulomb_metric()
+        res[limit] = gpu_eri(cuda, g, [f], 1)
+        g.close()
+    one, chunked = res[None], res[qc * per_q]
+    # the ERIs are returned in complex64: allow two fp32 ulps at the largest entry;
+    # the traces are reduced in FP64 from E itself
+    scale = np.abs(one[0][0]).max()
+    assert np.abs(chunked[0][0] - one[0][0]).max() <= 2.4e-7 * scale
+    assert abs(chunked[1][0] - one[1][0]) < 1e-10 and abs(chunked[2][0] - one[2][0]) < 1e-10
+    ref, (rj, rk) = o.eri(tol, f)
+    assert np.abs(chunked[0][0] - ref).max() < MIXED_TOL
+    assert abs(chunked[1][0] - rj) < MIXED_TOL and abs(chunked[2][0] - rk) < MIXED_TOL
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7)])
 def test_eri_c2(cuda, lib_built, c2, prec, tol):
     from paper_2601_16379_gb300 import binding as B
@@ -271,3 +333,56 @@ def test_errors_and_state(cuda, lib_built, c1):
     g.coulomb_metric()
     ej, ek = g.fragment_eri([])
     assert len(ej) == 0
+
+
+# ------------------------------------------------- Coulomb kernel from eta
+@pytest.mark.parametrize("case", ["c1", "aniso"])
+def test_eta_route_matches_oracle(cuda, lib_built, c1, aniso, case):
+    """isdf_coulomb_metric_eta (Eqs. 7-8) gives the fragment ERIs of the zeta
+    route (Eq. 6) within the FP64 tolerance at tau = 1e-8 (the eta route
+    multiplies rounding by cond(Pi^q), so it is used with a truncation)."""
+    from paper_2601_16379_gb300 import binding as B
+    tau = 1e-8
+    if case == "c1":
+        wl, o = c1
+        cell, n_p, seed = wl.cell, wl.n_p, wl.seed
+        frags = [wl.fragments[0], W.make_fragment(cell, seed, 5, 7)]
+    else:
+        cell, o = aniso
+        n_p, seed = 40, 99
+        frags = [W.make_fragment(cell, 5, 0, 5)]
+    g = B.Isdf(cell, B.ISDF_FP64)
+    g.build_points(n_p, seed)
+    g.fit_zeta(tau)
+    g.coulomb_metric_eta()
+    eris, ej, ek = gpu_eri(cuda, g, frags, 0)
+    for i, f in enumerate(frags):
+        ref, (rj, rk) = o.eri(tau, f)
+        assert np.abs(eris[i] - ref).max() < FP64_TOL
+        assert abs(ej[i] - rj) < FP64_TOL and abs(ek[i] - rk) < FP64_TOL
+
+
+# ------------------------------------------------------ exchange (Eq. 10)
+@pytest.mark.parametrize("case,tau", [("c1", 1e-7), ("aniso", 1e-12)])
+def test_exchange_matches_oracle(cuda, lib_built, c1, aniso, case, tau):
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    if case == "c1":
+        wl, o = c1
+        cell, n_p, seed = wl.cell, wl.n_p, wl.seed
+    else:
+        cell, o = aniso
+        n_p, seed = 40, 99
+    rng = np.random.default_rng(11)
+    Cs = rng.standard_normal((cell.nkpts, cell.nao, 3)) + 1j * rng.standard_normal((cell.nkpts, cell.nao, 3))
+    P = np.einsum("kmi,kni->kmn", Cs, Cs.conj()) / cell.nao
+    g = B.Isdf(cell, B.ISDF_FP64)
+    g.build_points(n_p, seed)
+    g.fit_zeta(tau)
+    g.coulomb_metric()
+    K = torch.empty((cell.nkpts, cell.nao, cell.nao), dtype=torch.complex128, device="cuda")
+    g.exchange(_dev(torch, P), K)
+    torch.cuda.synchronize()
+    _, _, V = o.fit(tau)
+    Ko = O.exchange_matrix(o.X, V, P, cell.kmesh)
+    assert np.abs(K.cpu().numpy() - Ko).max() < FP64_TOL
