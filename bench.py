@@ -266,10 +266,11 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     and extrapolate to one full build by exact operation counts.
 
     Sample: Bloch GTOs for 2 k-points; 6 pivots of the point selection on a
-    2-k-point Phi; Pi for 1 q; g and eta for 1 q on a grid slice; the solve and
-    Coulomb metric for 1 q on a grid slice / full grid; the pair tensor and E
-    for 1 q of the smallest and the largest fragment.  Each piece scales
-    linearly in the counted units it skips."""
+    2-k-point Phi; Pi, eta and the pair tensor for 1 q with their k-sums over a
+    2x2x2 sub-mesh (eta on a grid slice); the solve and Coulomb metric for 1 q
+    on a grid slice / full grid; E for 1 q of the smallest and the median
+    fragment.  Each piece scales linearly in the counted units it skips (the
+    number of k in a k-sum, of q, of grid points, of pivots)."""
     import oracle as O
     from paper_2601_16379_gb300 import workloads as W
 
@@ -289,16 +290,19 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     t_ip = _timeit(lambda: O.select_ips(phi2, 6, wl.seed))
     parts["select_ips"] = t_ip * (npp / 6) * (nk / 2)
     # S2: Pi (per q), g (per k), eta (per q, per grid point), solve (per q, per grid point)
-    X = crand(nk, npp, nao)
-    t_pi = _timeit(lambda: O.metric_pi(X, cell.kmesh, qs=[1]))
-    parts["metric_pi"] = t_pi * nk
+    # k-sums are timed over a sub-mesh of ks k-points and scaled by nk / ks
+    sub = tuple(min(2, n) for n in cell.kmesh)
+    ks = int(np.prod(sub))
+    X = crand(ks, npp, nao)
+    t_pi = _timeit(lambda: O.metric_pi(X, sub, qs=[min(1, ks - 1)]))
+    parts["metric_pi"] = t_pi * (nk / ks) * nk
     gs = max(1, ng // 64)
     phis = crand(2, nao, gs)
     t_g = _timeit(lambda: O.g_values(X[:2], phis))
     parts["g_values"] = t_g * (nk / 2) * (ng / gs)
-    gsl = crand(nk, npp, gs)
-    t_eta = _timeit(lambda: O.rhs_eta(X, None, cell.kmesh, qs=[1], g=gsl))
-    parts["rhs_eta"] = t_eta * nk * (ng / gs)
+    gsl = crand(ks, npp, gs)
+    t_eta = _timeit(lambda: O.rhs_eta(X, None, sub, qs=[min(1, ks - 1)], g=gsl))
+    parts["rhs_eta"] = t_eta * (nk / ks) * nk * (ng / gs)
     A = crand(npp, 2 * npp)
     Pi = (A @ A.conj().T)[None]
     t_fit = _timeit(lambda: O.fit_zeta(Pi, gsl[:1], SOLVE_TOL))
@@ -313,9 +317,9 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     samp = sorted(set([min(sizes), int(np.median(sizes))]))
     per = {}
     for nf in samp:
-        T = crand(nk, npp, nf)
-        t_m = _timeit(lambda: O.pair_tensor(T, cell.kmesh, qs=[1]))
-        M1 = O.pair_tensor(T, cell.kmesh, qs=[1])
+        T = crand(ks, npp, nf)
+        t_m = _timeit(lambda: O.pair_tensor(T, sub, qs=[min(1, ks - 1)])) * (nk / ks)
+        M1 = O.pair_tensor(T, sub, qs=[min(1, ks - 1)])
         t_e = _timeit(lambda: O.fragment_E(M1, V1, nk))
         per[nf] = (t_m, t_e)
     # fit t(nf) = a nf^2 + b nf^4 to the two sample sizes (per Q)
@@ -331,9 +335,10 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     total = sum(parts.values())
     cores = int(os.environ.get("OMP_NUM_THREADS", 0)) or len(os.sched_getaffinity(0))
     return {"value": total, "unit": "s", "cores": cores, "kind": "oracle", "extrapolated": True,
-            "sample": "oracle pieces timed on a bounded sample (2 k-points of Phi, 6 pivots, 1 q of Pi/eta/solve/V "
-                      "on a 1/64 grid slice, 1 q of the pair tensor and E for the smallest and the median fragment), "
-                      "scaled by exact operation counts to one full build",
+            "sample": "oracle pieces timed on a bounded sample (2 k-points of Phi, 6 pivots; 1 q of Pi, eta and the "
+                      "pair tensor with k-sums over a 2x2x2 sub-mesh, eta and the solve on a 1/64 grid slice; 1 q of "
+                      "V and of E for the smallest and the median fragment), scaled by exact operation counts to one "
+                      "full build",
             "parts_s": {k: round(v, 3) for k, v in parts.items()}}
 
 

@@ -170,14 +170,19 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb,
  * Needs the Coulomb metric (either route). */
 int isdf_exchange(isdf_handle* h, const void* P, void* K_out);
 
-/* Time-reversal pairing in isdf_fragment_eri (default on).  For a real AO
- * basis on a Gamma-centred k-mesh, V^{-q} = conj(V^q), and for any orbitals
- * M^{-q}_{(qp),I} = conj(M^q_{(pq),I}) (shift k by q in the k-sum of the
- * pair tensor, Eq. 20).  So the term
- * of -q in (pq|rs) = (1/Nk) sum_q [M^q V^q M^q^H] equals the term of q with
- * the pair indices swapped and conjugated, and the sum is taken over about
- * half of the q-points, then completed by that swap.  enable = 0 sums over all
- * q-points as written.  The results agree to rounding. */
+/* Time-reversal pairing (default on).  The AO basis is real and the k-mesh
+ * Gamma-centred, so Pi^{-q} = conj(Pi^q) and eta^{-q} = conj(eta^q) (Eqs. 4-5),
+ * hence zeta^{-q} = conj(zeta^q) and V^{-q} = conj(V^q); and for any orbitals
+ * M^{-q}_{(qp),I} = conj(M^q_{(pq),I}) (shift k by q in the k-sum of the pair
+ * tensor, Eq. 20).  With pairing on:
+ *   - isdf_fit_zeta and the Coulomb metric (both routes) compute the factor of
+ *     Pi^q, xi^q and V^q only for q <= -q (index order) and set the others to
+ *     the conjugates;
+ *   - isdf_fragment_eri sums (pq|rs) = (1/Nk) sum_q [M^q V^q M^q^H] over about
+ *     half of the q-points, since the term of -q is the term of q with the pair
+ *     indices swapped and conjugated.
+ * enable = 0 computes every q as written.  The results agree to rounding.
+ * The setting applies to the calls made after it. */
 int isdf_set_time_reversal(isdf_handle* h, int enable);
 
 /* MIXED mode: device bytes that the fragment contraction may use for the fp16

@@ -276,6 +276,35 @@ void q_point_set(const KMesh& km, bool pair, std::vector<int>& qs, std::vector<d
   }
 }
 
+// Representatives of the pairs {q, -q} (q <= -q in index order, self-conjugate
+// q included) in runs of consecutive q, and (dst, src) = (q, -q) for the rest.
+// For a real AO basis on a Gamma-centred mesh Pi^{-q} = conj(Pi^q) and
+// eta^{-q} = conj(eta^q), so the factor, xi and V_xi of -q are the conjugates
+// of those of q.  Without pairing every q is its own representative.
+struct QHalf {
+  std::vector<std::pair<int, int>> runs;  // (first q, count)
+  std::vector<int2> mirror;               // (q, -q) for q not computed
+  int count = 0;                          // computed q-points
+};
+QHalf fit_q_set(const KMesh& km, bool pair) {
+  const int n0 = km.n[0], n1 = km.n[1], n2 = km.n[2], nk = n0 * n1 * n2;
+  QHalf h;
+  for (int q = 0; q < nk; ++q) {
+    const int m0 = q / (n1 * n2), m1 = (q / n2) % n1, m2 = q % n2;
+    const int mq = (((n0 - m0) % n0) * n1 + (n1 - m1) % n1) * n2 + (n2 - m2) % n2;
+    if (pair && mq < q) {
+      h.mirror.push_back(make_int2(q, mq));
+      continue;
+    }
+    ++h.count;
+    if (!h.runs.empty() && h.runs.back().first + h.runs.back().second == q)
+      ++h.runs.back().second;
+    else
+      h.runs.push_back({q, 1});
+  }
+  return h;
+}
+
 double frag_m_flops(int nk, int np, int nf, int nao, const KMesh& km) {
   const double per_pt = 8.0 * (km.n[0] + km.n[1] + km.n[2]);
   return 8.0 * nk * (double)np * nf * nao + per_pt * nk * (double)np * nf + 6.0 * nk * (double)nf * nf * np +
@@ -564,8 +593,9 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
   const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
   double2* X = (double2*)h->buf("X");
   double2* phi = (double2*)h->buf("phi");
-  // algorithmic work: g^k GEMM + eta k-convolutions + xi = W eta (complex flops x 8)
-  StageTimer stt(h, 1, 8.0 * nk * (double)np * ng * (nao + np));
+  const QHalf qh = fit_q_set(km, h->q_sym);
+  // algorithmic work: g^k GEMM (all k) + xi = W eta (triangular) at the computed q
+  StageTimer stt(h, 1, 8.0 * nk * (double)np * ng * nao + 4.0 * qh.count * (double)np * np * ng);
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   // Pi^q (Eq. 4): G^k_IJ = sum_mu conj(X^k_I mu) X^k_J mu, then the k-convolution
   ENSURE(Pi, double2, "Pi", (size_t)nk * np * np);
@@ -582,17 +612,30 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
   ENSURE(permPi, int32_t, "permPi", (size_t)nk * np);
   ENSURE(rankPi, int32_t, "rankPi", nk);
   ENSURE(dwork, double, "chol_dwork", (size_t)nk * 2 * np);
-  CK(pchol_batched(h->st, Pi, np, nk, solve_tol, LtPi, permPi, rankPi, dwork));
   ENSURE(W, double2, "W", (size_t)nk * np * np);
   ENSURE(wwork, double2, "W_work", (size_t)nk * np * np);
-  CK(trinv_batched(h->st, LtPi, permPi, rankPi, np, nk, W, wwork));
-  // xi^q = W eta^q = L_S^{-1} (eta^q rows in pivot order): triangular, gathered
   ENSURE(xi, double2, "xi", (size_t)nk * np * ng);
-  CK(ztrmm_gather(h->st, np, ng, wwork, np, (int64_t)np * np, permPi, np, eta, ng, (int64_t)np * ng, xi, ng,
-                  (int64_t)np * ng, nk));
+  const int64_t pp = (int64_t)np * np, pg = (int64_t)np * ng;
+  for (const auto& r : qh.runs) {
+    const int q0 = r.first, nq = r.second;
+    CK(pchol_batched(h->st, Pi + q0 * pp, np, nq, solve_tol, LtPi + q0 * pp, permPi + (int64_t)q0 * np,
+                     rankPi + q0, dwork + (int64_t)q0 * 2 * np));
+    CK(trinv_batched(h->st, LtPi + q0 * pp, permPi + (int64_t)q0 * np, rankPi + q0, np, nq, W + q0 * pp,
+                     wwork + q0 * pp));
+    // xi^q = W eta^q = L_S^{-1} (eta^q rows in pivot order): triangular, gathered
+    CK(ztrmm_gather(h->st, np, ng, wwork + q0 * pp, np, pp, permPi + (int64_t)q0 * np, np, eta + q0 * pg, ng, pg,
+                    xi + q0 * pg, ng, pg, nq));
+  }
+  if (!qh.mirror.empty()) {
+    ENSURE(mir, int2, "q_mirror", qh.mirror.size());
+    CK(cudaMemcpyAsync(mir, qh.mirror.data(), sizeof(int2) * qh.mirror.size(), cudaMemcpyHostToDevice, h->st));
+    CK(mirror_conj(h->st, W, pp, mir, (int)qh.mirror.size()));
+    CK(mirror_conj(h->st, xi, pg, mir, (int)qh.mirror.size()));
+  }
   h->ranks.assign(nk, 0);
   CK(cudaMemcpyAsync(h->ranks.data(), rankPi, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  for (const int2& m : qh.mirror) h->ranks[m.x] = h->ranks[m.y];
   if (rank_out) std::memcpy(rank_out, h->ranks.data(), sizeof(int32_t) * nk);
   for (int q = 0; q < nk; ++q)
     if (h->ranks[q] < 1) return fail(h, ISDF_ERR_NUMERIC, "Pi^q has rank 0 at q=%d", q);
@@ -613,24 +656,36 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
   double2* xi = (double2*)h->buf("xi");
   double2* W = (double2*)h->buf("W");
   const double2* tw = (const double2*)h->buf("grid_tw");
-  StageTimer stt(h, 2, 4.0 * nk * (double)np * np * ng);  // Hermitian V_xi GEMM
+  const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
+  const QHalf qh = fit_q_set(km, h->q_sym);
+  StageTimer stt(h, 2, 4.0 * qh.count * (double)np * np * ng);  // Hermitian V_xi GEMM
   ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
   ENSURE(gwork, uint8_t, "grid_work", grid_coulomb_work_bytes(nk, h->cell));
+  const int64_t pp = (int64_t)np * np, pg = (int64_t)np * ng;
   if (h->prec == ISDF_FP64) {
-    CK(grid_coulomb_fft(h->st, xi, np, 0, nk, h->cell, tw, gwork));
-    CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi, ng, (int64_t)np * ng, xi, ng,
-             (int64_t)np * ng, zero, Vxi, np, (int64_t)np * np, nk));
+    for (const auto& r : qh.runs) {
+      CK(grid_coulomb_fft(h->st, xi + r.first * pg, np, r.first, r.second, h->cell, tw, gwork));
+      CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi + r.first * pg, ng, pg,
+               xi + r.first * pg, ng, pg, zero, Vxi + r.first * pp, np, pp, r.second));
+    }
   } else {
     // V_xi in complex64 with compensated accumulation: xi is well scaled (|xi| ~ |rho|), and
     // an error in V_xi reaches E as P dV_xi P^H with P = M W^T well scaled, i.e. relative to
     // |E| (the ill-conditioned factor W is applied afterwards, in FP64).
     ENSURE(xif, float2, "xi_f", (size_t)nk * np * ng);
     ENSURE(Vxif, float2, "Vxi_f", (size_t)nk * np * np);
-    CK(z2c(h->st, xi, xif, (int64_t)nk * np * ng));
-    CK(grid_coulomb_fft_f(h->st, xif, np, 0, nk, h->cell, tw, gwork));
-    CK(cgemm(h->st, 'R', 'T', np, np, ng, make_float2((float)h->volume, 0.f), xif, ng, (int64_t)np * ng, xif, ng,
-             (int64_t)np * ng, make_float2(0.f, 0.f), Vxif, np, (int64_t)np * np, nk));
-    CK(c2z(h->st, Vxif, Vxi, (int64_t)nk * np * np));
+    for (const auto& r : qh.runs) {
+      CK(z2c(h->st, xi + r.first * pg, xif + r.first * pg, r.second * pg));
+      CK(grid_coulomb_fft_f(h->st, xif + r.first * pg, np, r.first, r.second, h->cell, tw, gwork));
+      CK(cgemm(h->st, 'R', 'T', np, np, ng, make_float2((float)h->volume, 0.f), xif + r.first * pg, ng, pg,
+               xif + r.first * pg, ng, pg, make_float2(0.f, 0.f), Vxif + r.first * pp, np, pp, r.second));
+      CK(c2z(h->st, Vxif + r.first * pp, Vxi + r.first * pp, r.second * pp));
+    }
+  }
+  if (!qh.mirror.empty()) {
+    ENSURE(mir, int2, "q_mirror", qh.mirror.size());
+    CK(cudaMemcpyAsync(mir, qh.mirror.data(), sizeof(int2) * qh.mirror.size(), cudaMemcpyHostToDevice, h->st));
+    CK(mirror_conj(h->st, Vxi, pp, mir, (int)qh.mirror.size()));
   }
   h->has_xi = false;  // xi was transformed in place (FP64) / is no longer needed
   return coulomb_tail(h, Vxi, V_out);
@@ -653,15 +708,26 @@ int isdf_coulomb_metric_eta(isdf_handle* h, void* V_out) {
   double2* W = (double2*)h->buf("W");
   double2* work = (double2*)h->buf("xi");  // the copy of eta is transformed in place
   const double2* tw = (const double2*)h->buf("grid_tw");
-  StageTimer stt(h, 2, 4.0 * nk * (double)np * np * ng);
+  const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
+  const QHalf qh = fit_q_set(km, h->q_sym);
+  StageTimer stt(h, 2, 4.0 * qh.count * (double)np * np * ng);
   ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
   ENSURE(Veta, double2, "Veta", (size_t)nk * np * np);
   ENSURE(gwork, uint8_t, "grid_work", grid_coulomb_work_bytes(nk, h->cell));
-  CK(cudaMemcpyAsync(work, eta, sizeof(double2) * (size_t)nk * np * ng, cudaMemcpyDeviceToDevice, h->st));
   h->has_xi = false;
-  CK(grid_coulomb_fft(h->st, work, np, 0, nk, h->cell, tw, gwork));
-  CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), work, ng, (int64_t)np * ng, work, ng,
-           (int64_t)np * ng, zero, Veta, np, (int64_t)np * np, nk));
+  const int64_t pp = (int64_t)np * np, pg = (int64_t)np * ng;
+  for (const auto& r : qh.runs) {
+    CK(cudaMemcpyAsync(work + r.first * pg, eta + r.first * pg, sizeof(double2) * (size_t)(r.second * pg),
+                       cudaMemcpyDeviceToDevice, h->st));
+    CK(grid_coulomb_fft(h->st, work + r.first * pg, np, r.first, r.second, h->cell, tw, gwork));
+    CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), work + r.first * pg, ng, pg,
+             work + r.first * pg, ng, pg, zero, Veta + r.first * pp, np, pp, r.second));
+  }
+  if (!qh.mirror.empty()) {
+    ENSURE(mir, int2, "q_mirror", qh.mirror.size());
+    CK(cudaMemcpyAsync(mir, qh.mirror.data(), sizeof(int2) * qh.mirror.size(), cudaMemcpyHostToDevice, h->st));
+    CK(mirror_conj(h->st, Veta, pp, mir, (int)qh.mirror.size()));
+  }
   // V_xi = conj(W) (V_eta W^T)
   double2* tmp = (double2*)h->ensure("W_work", sizeof(double2) * (size_t)nk * np * np);
   if (!tmp) return fail(h, ISDF_ERR_OOM, "workspace");
@@ -790,7 +856,8 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
             const int nq = std::min(qc, r.first + r.second - q0);
             CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M + q0 * sq, np, sq, Lwf + q0 * pp, np, pp, zero, Bc,
                      np, sq, nq));
-            CK(cudaMemcpyAsync(M + q0 * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(M + q0 * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice,
+                               h->st));
           }
       }
       {

@@ -89,6 +89,108 @@ __device__ void kmesh_dft_smem(T* s, int ct, const int n[3], const typename CT<T
   }
 }
 
+// The same for a cubic mesh of compile-time side L: the twiddle indices are
+// compile-time constants, so the L twiddles of the pass live in registers, and
+// ct is a power of two (lct = log2 ct).
+template <typename T, int L>
+__device__ void kmesh_dft_cubic(T* s, int lct, const typename CT<T>::R* tcs, const typename CT<T>::R* tss) {
+  using R = typename CT<T>::R;
+  R wc[L], ws[L];
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    wc[t] = tcs[t];
+    ws[t] = tss[t];
+  }
+  const int ct = 1 << lct, nlines = L * L * ct;
+#pragma unroll
+  for (int a = 2; a >= 0; --a) {
+    const int stride = (a == 2) ? 1 : (a == 1 ? L : L * L);
+    for (int line = threadIdx.x; line < nlines; line += blockDim.x) {
+      const int c = line & (ct - 1);
+      const int rest = line >> lct;
+      const int hi = rest / stride, lo = rest % stride;
+      const int base = hi * stride * L + lo;
+      T v[L];
+#pragma unroll
+      for (int i = 0; i < L; ++i) v[i] = s[((base + i * stride) << lct) + c];
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        R ax = 0, ay = 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+          const int t = (i * j) % L;
+          ax += v[i].x * wc[t] - v[i].y * ws[t];
+          ay += v[i].x * ws[t] + v[i].y * wc[t];
+        }
+        s[((base + j * stride) << lct) + c] = CT<T>::mk(ax, ay);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, int64_t ncol, int lct, int mode,
+                                                         Twiddles16 tw1, Twiddles16 tw2, double scale) {
+  using R = typename CT<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  __shared__ R tw1c[16], tw1s[16], tw2c[16], tw2s[16];
+  for (int t = threadIdx.x; t < 16; t += blockDim.x) {
+    tw1c[t] = (R)tw1.c[0][t];
+    tw1s[t] = (R)tw1.s[0][t];
+    tw2c[t] = (R)tw2.c[0][t];
+    tw2s[t] = (R)tw2.s[0][t];
+  }
+  constexpr int nk = L * L * L;
+  const int ct = 1 << lct;
+  const int64_t c0 = (int64_t)blockIdx.x << lct;
+  for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+    const int k = e >> lct, c = e & (ct - 1);
+    const int64_t col = c0 + c;
+    T v = CT<T>::mk(0, 0);
+    if (col < ncol) v = data[(int64_t)k * ncol + col];
+    s[e] = v;
+  }
+  __syncthreads();
+  kmesh_dft_cubic<T, L>(s, lct, tw1c, tw1s);
+  if (mode == 1) {
+    for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+      T v = s[e];
+      s[e] = CT<T>::mk(v.x * v.x + v.y * v.y, 0);
+    }
+    __syncthreads();
+    kmesh_dft_cubic<T, L>(s, lct, tw2c, tw2s);
+  }
+  for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+    const int k = e >> lct, c = e & (ct - 1);
+    const int64_t col = c0 + c;
+    if (col < ncol) {
+      T v = s[e];
+      data[(int64_t)k * ncol + col] = CT<T>::mk(v.x * (R)scale, v.y * (R)scale);
+    }
+  }
+}
+
+template <typename T, int L>
+cudaError_t kdft_cubic_launch(cudaStream_t st, T* data, int64_t ncol, int mode, const Twiddles16& t1,
+                              const Twiddles16& t2, double scale) {
+  constexpr int nk = L * L * L;
+  int lct = 0;
+  while (lct < 5 && ((int64_t)nk * sizeof(T) << (lct + 1)) <= 65536) ++lct;
+  const size_t smem = (size_t)nk * sizeof(T) << lct;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kdft_cubic_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t nblk = (ncol + (1 << lct) - 1) >> lct;
+  if (nblk > 2147483647LL) return cudaErrorInvalidValue;
+  kdft_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, lct, mode, t1, t2, scale);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) kdft_cols_kernel(T* __restrict__ data, int64_t ncol, KMesh km,
                                                         int ct, int mode, Twiddles16 tw1,
@@ -139,6 +241,18 @@ cudaError_t kdft_launch(cudaStream_t st, T* data, int64_t ncol, KMesh km, int s1
   for (int a = 0; a < 3; ++a)
     if (km.n[a] < 1 || km.n[a] > 16) return cudaErrorInvalidValue;
   if (ncol <= 0) return cudaSuccess;
+  if (km.n[0] == km.n[1] && km.n[1] == km.n[2]) {
+    const Twiddles16 t1 = make_tw(km.n, s1), t2 = make_tw(km.n, s2);
+    switch (km.n[0]) {
+      case 2: return kdft_cubic_launch<T, 2>(st, data, ncol, mode, t1, t2, scale);
+      case 3: return kdft_cubic_launch<T, 3>(st, data, ncol, mode, t1, t2, scale);
+      case 4: return kdft_cubic_launch<T, 4>(st, data, ncol, mode, t1, t2, scale);
+      case 6: return kdft_cubic_launch<T, 6>(st, data, ncol, mode, t1, t2, scale);
+      case 8: return kdft_cubic_launch<T, 8>(st, data, ncol, mode, t1, t2, scale);
+      case 10: return kdft_cubic_launch<T, 10>(st, data, ncol, mode, t1, t2, scale);
+      default: break;
+    }
+  }
   int ct = (int)(65536 / ((int64_t)nk * sizeof(T)));
   if (ct < 1) ct = 1;
   if (ct > 32) ct = 32;

@@ -145,6 +145,20 @@ __global__ void scale_blocks_kernel(const double2* __restrict__ L, int64_t per, 
   }
 }
 
+// x[dst] = conj(x[src]) (or a plain copy) for blocks of `per` elements, over
+// a list of (dst, src) block pairs.
+template <typename T, bool kConj>
+__global__ void mirror_kernel(T* __restrict__ x, int64_t per, const int2* __restrict__ pairs, int npairs) {
+  const int64_t total = per * npairs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int2 pr = pairs[e / per];
+    const int64_t j = e % per;
+    T v = x[(int64_t)pr.y * per + j];
+    if constexpr (kConj) v.y = -v.y;
+    x[(int64_t)pr.x * per + j] = v;
+  }
+}
+
 __global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = make_float2((float)in[e].x, (float)in[e].y);
@@ -218,6 +232,13 @@ cudaError_t scale_blocks(cudaStream_t st, const double2* L, int64_t per, int nb,
 }
 cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, float2* out) {
   scale_blocks_kernel<float2><<<nblocks(per * nb), 256, 0, st>>>(L, per, nb, sw, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mirror_conj(cudaStream_t st, double2* x, int64_t per, const int2* pairs, int npairs) {
+  if (npairs <= 0 || per <= 0) return cudaSuccess;
+  mirror_kernel<double2, true><<<nblocks(per * npairs), 256, 0, st>>>(x, per, pairs, npairs);
   count_launch();
   return cudaGetLastError();
 }

@@ -256,6 +256,26 @@ def test_mixed_q_chunks_c2(cuda, lib_built, c2, qc):
     assert abs(chunked[1][0] - rj) < MIXED_TOL and abs(chunked[2][0] - rk) < MIXED_TOL
 
 
+def test_mixed_large_np_matches_fp64(cuda, lib_built):
+    """N_P = 520 puts B = M L (K' = 2 N_P > 1024) on the compensated SIMT GEMM
+    instead of the exact-slice tensor kernel; the mixed ERIs and traces still
+    match the FP64 path (itself pinned to the oracle) within the mixed bound."""
+    from paper_2601_16379_gb300 import binding as B
+    wl = W.workload("c3", kmesh=2, mesh=24, n_p=520, frag_sizes=[6, 9])
+    res = {}
+    for prec in (B.ISDF_FP64, B.ISDF_MIXED):
+        g = B.Isdf(wl.cell, prec)
+        g.build_points(wl.n_p, wl.seed)
+        g.fit_zeta(1e-7)
+        g.coulomb_metric()
+        res[prec] = gpu_eri(cuda, g, wl.fragments, prec)
+        g.close()
+    d, m = res[B.ISDF_FP64], res[B.ISDF_MIXED]
+    for i in range(len(wl.fragments)):
+        assert np.abs(m[0][i] - d[0][i]).max() < MIXED_TOL
+        assert abs(m[1][i] - d[1][i]) < MIXED_TOL and abs(m[2][i] - d[2][i]) < MIXED_TOL
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7)])
 def test_eri_c2(cuda, lib_built, c2, prec, tol):
     from paper_2601_16379_gb300 import binding as B
