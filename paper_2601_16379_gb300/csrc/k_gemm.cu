@@ -71,7 +71,7 @@ __device__ __forceinline__ float2 finish(float2 acc, float2 lo) {
 // op(A); brow (with batch stride sIdx) gathers the rows of B ('N' only):
 // op(B)[kk][n] = B[brow[kk]][n], 0 where brow[kk] < 0.
 template <typename T, int BK>
-__global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, int n, int k, T alpha,
+__global__ void __launch_bounds__(256, 2) gemm_kernel(char opA, char opB, int m, int n, int k, T alpha,
                                                    const T* __restrict__ A, int64_t lda, int64_t sA,
                                                    const T* __restrict__ B, int64_t ldb, int64_t sB,
                                                    T beta, T* __restrict__ C, int64_t ldc,
@@ -104,9 +104,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
       lo[i][j] = zero_c<T>();
     }
 
-  for (int k0 = 0; k0 < kend; k0 += BK) {
-    // load op(A) tile: BM x BK
-    for (int e = tid; e < BM * BK; e += 256) {
+  // Global -> register staging of one K-tile (op(A): BM x BK, op(B): BK x BN), so
+  // that the loads of tile k0 + BK are in flight while tile k0 is computed.
+  constexpr int NA = (BM * BK) / 256, NB = (BN * BK) / 256;
+  T ra[NA], rb[NB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int e = tid + u * 256;
       int mm, kk;
       if (aT) {
         kk = e / BM;
@@ -118,10 +123,11 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
       const int gm = m0 + mm, gk = k0 + kk;
       T v = zero_c<T>();
       if (gm < m && gk < k) v = aT ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-      As[kk][mm] = conj_if(v, aC);
+      ra[u] = conj_if(v, aC);
     }
-    // load op(B) tile: BK x BN
-    for (int e = tid; e < BN * BK; e += 256) {
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int e = tid + u * 256;
       int nn, kk;
       if (bT) {
         nn = e / BK;
@@ -140,8 +146,31 @@ __global__ void __launch_bounds__(256) gemm_kernel(char opA, char opB, int m, in
           v = bT ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
         }
       }
-      Bs[kk][nn] = conj_if(v, bC);
+      rb[u] = conj_if(v, bC);
     }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int e = tid + u * 256;
+      if (aT)
+        As[e / BM][e % BM] = ra[u];
+      else
+        As[e % BK][e / BK] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int e = tid + u * 256;
+      if (bT)
+        Bs[e % BK][e / BK] = rb[u];
+      else
+        Bs[e / BN][e % BN] = rb[u];
+    }
+  };
+  if (kend > 0) fetch(0);
+  for (int k0 = 0; k0 < kend; k0 += BK) {
+    stash();
+    if (k0 + BK < kend) fetch(k0 + BK);
     __syncthreads();
     if constexpr (kComp) {
       T part[4][4];

@@ -16,7 +16,8 @@
 // slices are integers, and the three weight groups
 //     g0 = S1.T1,  g1 = S1.T2 + S2.T1,  g2 = S1.T3 + S2.T2 + S3.T1
 // are accumulated in FP32 TMEM.  g0 carries weight 1 and must be exact: a
-// chunk of 48 k-steps keeps its partial sums integers below 2^24, so the FP32
+// chunk of 64 k-steps (1024 products of magnitude <= 2^14) keeps its partial
+// sums integers of magnitude at most 2^24, so the FP32
 // accumulation is exact whatever its rounding; g0 is double-buffered and each
 // chunk is drained (overlapping the next chunk's MMAs) into a float-float
 // (TwoSum) accumulator in global memory.  g1 and g2 carry weights 2^-7 and
@@ -51,7 +52,7 @@ constexpr int B_BYTES = BN * BK * 2;        // 16 KB per slice
 constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);  // 96 KB
 constexpr int TMEM_COLS = 512;              // g0 (two buffers), g1, g2: four 128-column FP32 accumulators
 constexpr int NTHREADS = 192;
-constexpr int kChunkKB = 12;                // k-blocks per exact g0 chunk: 48 k-steps of 16
+constexpr int kChunkKB = 16;                // k-blocks per exact g0 chunk: 64 k-steps of 16
 constexpr int kP1 = 4;                      // chunks per g1 drain
 constexpr int kP2 = 16;                     // chunks per g2 drain
 constexpr unsigned long long kWaitNs = 4000000000ULL;  // bounded waits: 4 s of device time
