@@ -129,7 +129,7 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     prec = B.ISDF_MIXED if args.precision == "mixed" else B.ISDF_FP64
-    wl = W.workload(args.workload)
+    wl = W.workload(args.workload, kmesh=args.kmesh, mesh=args.mesh, frag_sizes=_frag_sizes(args))
     frags = wl.fragments
     g = B.Isdf(wl.cell, prec)
     dt_out = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
@@ -231,7 +231,7 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f64 fit + f32/fp16-slice fragment contraction" if prec == B.ISDF_MIXED else "f64",
         "data": "synthetic (seeded cell, Gaussian basis and fragment orbitals)",
-        "config": {"workload": f"{args.workload}: {wl.description}", "precision": args.precision,
+        "config": {"workload": f"{args.workload}: {wl.description}" + _overrides(args), "precision": args.precision,
                    "solve_tol": args.solve_tol, "fragments": len(frags),
                    "sum_nf4": int(sum(f.norb ** 4 for f in frags)),
                    "l2": "inputs larger than L2 (Phi, eta, xi, M, B each > 129 MB)",
@@ -249,12 +249,91 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk,
         "traces_fragment0": {"E_J": float(ej[0]), "E_K": float(ek[0])},
     }
+    if rank == 0 and prec == B.ISDF_MIXED and not args.no_accuracy:
+        # outside the timed region: free this handle's HBM, then compare against the FP64 path
+        del outs
+        g.close()
+        torch.cuda.empty_cache()
+        result["accuracy"] = accuracy_vs_fp64(wl, args.solve_tol)
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
+        result["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget, kmesh=args.kmesh,
+                                              mesh=args.mesh, frag_sizes=_frag_sizes(args))
     if rank == 0:
         print(json.dumps(result))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _frag_sizes(args):
+    return [int(x) for x in args.frag_sizes.split(",")] if args.frag_sizes else None
+
+
+def _overrides(args):
+    o = []
+    if args.kmesh:
+        o.append(f"k-mesh {args.kmesh}^3")
+    if args.mesh:
+        o.append(f"grid {args.mesh}^3")
+    if args.frag_sizes:
+        o.append(f"fragments n_f = {args.frag_sizes}")
+    return f" (overridden: {', '.join(o)})" if o else ""
+
+
+# ------------------------------------------------ mixed vs FP64 accuracy
+FP64_FLOP_BUDGET = 3e13   # FP64 E = B B^H work per sampled fragment (~25 s at 1.2 TFLOP/s)
+
+
+def _paired_q_count(kmesh):
+    """Number of q-points the paired fragment contraction visits."""
+    n0, n1, n2 = kmesh
+    cnt = 0
+    for m0 in range(n0):
+        for m1 in range(n1):
+            self0 = m0 == 0 or 2 * m0 == n0
+            if 2 * m0 <= n0 and (not self0 or 2 * m1 <= n1):
+                cnt += n2
+    return cnt
+
+
+def accuracy_vs_fp64(wl, solve_tol):
+    """Max-abs ERI error and |dE_J|, |dE_K| (Ha) of the mixed path against the
+    FP64 path on the same GPU, for the smallest fragment and the largest one
+    whose FP64 contraction fits FP64_FLOP_BUDGET."""
+    import torch
+    from paper_2601_16379_gb300 import binding as B
+
+    cell, np_ = wl.cell, wl.n_p
+    nsum = _paired_q_count(cell.kmesh)
+    sizes = [f.norb for f in wl.fragments]
+    ok = [i for i, s in enumerate(sizes) if 4.0 * (s * s) ** 2 * nsum * np_ <= FP64_FLOP_BUDGET]
+    pick = sorted({int(np.argmin(sizes))} | ({max(ok, key=lambda i: sizes[i])} if ok else set()))
+    frags = [wl.fragments[i] for i in pick]
+    res = {}
+    for prec in (B.ISDF_FP64, B.ISDF_MIXED):
+        g = B.Isdf(cell, prec)
+        g.build_points(np_, wl.seed)
+        g.fit_zeta(solve_tol)
+        g.coulomb_metric()
+        dt = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
+        Cs = [torch.from_numpy(f.C).cuda() for f in frags]
+        gs = [torch.from_numpy(f.gamma).cuda() for f in frags]
+        outs = [torch.empty((f.norb,) * 4, dtype=dt, device="cuda") for f in frags]
+        ej, ek = g.fragment_eri(Cs, gs, outs)
+        torch.cuda.synchronize()
+        res[prec] = ([o.cpu().numpy().astype(np.complex128) for o in outs], ej, ek)
+        del outs, Cs, gs
+        g.close()
+        torch.cuda.empty_cache()
+    d, m = res[B.ISDF_FP64], res[B.ISDF_MIXED]
+    per = []
+    for i, f in enumerate(frags):
+        per.append({"n_f": f.norb, "max_abs_eri": float(np.abs(m[0][i] - d[0][i]).max()),
+                    "dE_J": float(abs(m[1][i] - d[1][i])), "dE_K": float(abs(m[2][i] - d[2][i])),
+                    "E_J": float(d[1][i]), "E_K": float(d[2][i])})
+    worst = max(max(x["max_abs_eri"], x["dE_J"], x["dE_K"]) for x in per)
+    return {"reference": "FP64 path on the same GPU (pinned to the FP64 oracle by the parity tests)",
+            "unit": "Ha", "tolerance": 1e-6, "max_error": worst, "within_tolerance": bool(worst <= 1e-6),
+            "fragments": per}
 
 
 # ------------------------------------------------------- CPU oracle sample
@@ -265,7 +344,7 @@ def _timeit(fn, repeat=1):
     return (time.perf_counter() - t0) / repeat
 
 
-def cpu_baseline(workload: str, budget_s: float = 20.0):
+def cpu_baseline(workload: str, budget_s: float = 20.0, kmesh=None, mesh=None, frag_sizes=None):
     """Time the FP64 oracle (as it stands) on a bounded sample of the workload
     and extrapolate to one full build by exact operation counts.
 
@@ -278,7 +357,7 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     import oracle as O
     from paper_2601_16379_gb300 import workloads as W
 
-    wl = W.workload(workload, with_fragments=False)
+    wl = W.workload(workload, kmesh=kmesh, mesh=mesh, frag_sizes=frag_sizes, with_fragments=False)
     cell = wl.cell
     nk, nao, ng, npp = cell.nkpts, cell.nao, cell.ngrid, wl.n_p
     rng = np.random.default_rng(0)
@@ -315,7 +394,7 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     t_v = _timeit(lambda: O.coulomb_metric(cell, z1, [1]))
     parts["coulomb_metric"] = t_v * nk
     # S4: pair tensor (per Q, ~n_f^2) and E (per Q, n_f^2 N_P^2 + n_f^4 N_P)
-    sizes = W.workload(workload, with_fragments=False).frag_sizes
+    sizes = wl.frag_sizes
     V1 = crand(1, npp, npp)
     t4 = 0.0
     samp = sorted(set([min(sizes), int(np.median(sizes))]))
@@ -351,10 +430,10 @@ def run_reference(args, rank):
         return
     t0 = time.perf_counter()
     for _ in range(args.warmup):
-        cpu_baseline(args.workload)
+        cpu_baseline(args.workload, kmesh=args.kmesh, mesh=args.mesh, frag_sizes=_frag_sizes(args))
     vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.workload))
+        vals.append(cpu_baseline(args.workload, kmesh=args.kmesh, mesh=args.mesh, frag_sizes=_frag_sizes(args)))
     v = float(np.median([x["value"] for x in vals]))
     base = vals[-1]
     base["value"] = v
@@ -379,6 +458,11 @@ def main():
     ap.add_argument("--solve-tol", type=float, default=SOLVE_TOL)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed vs FP64 comparison")
+    ap.add_argument("--kmesh", type=int, default=None, help="k-mesh side override (Nk scan)")
+    ap.add_argument("--mesh", type=int, default=None, help="real-space grid side override (small profiling cases)")
+    ap.add_argument("--frag-sizes", type=str, default=None,
+                    help="comma-separated fragment sizes replacing the workload's (small profiling cases)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -143,8 +143,10 @@ int isdf_coulomb_metric_eta(isdf_handle* h, void* V_out);
  *   C[f]       device complex128 [Nk][N_AO][n_orb[f]]
  *   gamma[f]   device complex128 [n_orb][n_orb] Hermitian density matrix with
  *              density n = sum_pq gamma_pq phi_p^* phi_q; array or entry may be NULL
- *   eri_out[f] device complex128 [p][q][r][s] chemist's (pq|rs) in FP64 mode,
- *              complex64 in MIXED mode; array or entry may be NULL
+ *   eri_out[f] complex128 [p][q][r][s] chemist's (pq|rs) in FP64 mode,
+ *              complex64 in MIXED mode; device memory or page-locked host
+ *              memory (written by the kernel over the host link, e.g. when the
+ *              ERIs of all fragments exceed HBM); array or entry may be NULL
  *   ej_out[f]  E_J = 1/2 sum gamma_pq gamma_rs (pq|rs)          (host, may be NULL)
  *   ek_out[f]  E_K = -1/4 sum gamma_ps gamma_rq (pq|rs)         (host, may be NULL)
  * The traces are accumulated in FP64.  Fragments are done one after the

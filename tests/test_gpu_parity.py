@@ -276,6 +276,29 @@ def test_mixed_large_np_matches_fp64(cuda, lib_built):
         assert abs(m[1][i] - d[1][i]) < MIXED_TOL and abs(m[2][i] - d[2][i]) < MIXED_TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eri_out_in_pinned_host_memory(cuda, lib_built, c1, prec):
+    """eri_out may be page-locked host memory: the result equals the device one."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, o = c1
+    f = W.make_fragment(wl.cell, wl.seed, 5, 7)
+    g = B.Isdf(wl.cell, prec)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(1e-7)
+    g.coulomb_metric()
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    C, gm = _dev(torch, f.C), _dev(torch, f.gamma)
+    dev = torch.empty((f.norb,) * 4, dtype=dt, device="cuda")
+    host = torch.empty((f.norb,) * 4, dtype=dt).pin_memory()
+    ej1, ek1 = g.fragment_eri([C], [gm], [dev])
+    ej2, ek2 = g.fragment_eri([C], [gm], [host])
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), host.numpy())
+    assert ej1[0] == ej2[0] and ek1[0] == ek2[0]
+    g.close()
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7)])
 def test_eri_c2(cuda, lib_built, c2, prec, tol):
     from paper_2601_16379_gb300 import binding as B
