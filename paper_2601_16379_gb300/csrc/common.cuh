@@ -167,6 +167,19 @@ cudaError_t herk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t 
                           int ntiles, void* ws, int accumulate, int* err);
 cudaError_t herk_tc_finish(cudaStream_t st, const void* ws, const int2* tiles_d, int ntiles, int64_t n2,
                            const int* row_exp, double scale, double2* E);
+// B^q = M^q L^q (w_q^{1/2} folded into L) on the tensor cores with four exact
+// integer slices, written in place over M^q.  prepare: slices of L for all q
+// (once per L); chunk: the q-points j0..j0+nq-1 of the sum (slot qmap[j]).
+int mlgemm_tc_kp(int np);
+int mlgemm_tc_np_pad(int np);
+bool mlgemm_tc_supported(int np);
+size_t mlgemm_tc_lslice_bytes(int nk, int np);
+size_t mlgemm_tc_split_bytes(int64_t n2, int np, int nq);
+cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, void* lsl,
+                              int* col_exp);
+cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* qmap, int64_t n2, int np, int j0,
+                            int nq, const int* row_exp, void* split, const void* lsl, const int* col_exp, int nk,
+                            int* err);
 // eri[p][q][r][s] (complex64) = E[(p q)][(s r)] (complex128) * scale
 cudaError_t eri_permute_zc(cudaStream_t st, const double2* E, int nf, double scale, float2* eri);
 

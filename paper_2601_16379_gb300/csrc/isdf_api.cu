@@ -820,26 +820,50 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     } else {
       const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
       float2* Xf = (float2*)h->buf("X_f");
-      ENSURE(Lwf, float2, "frag_Lwf", (size_t)nk * pp);
+      // B = M L on the tensor cores (four exact slices) when 2 N_P fits their exact
+      // accumulation, else on the compensated SIMT GEMM
+      const bool tc_ml = mlgemm_tc_supported(np);
+      float2* Lwf = nullptr;
+      void* lsl = nullptr;
+      int* lexp = nullptr;
+      if (tc_ml) {
+        lsl = h->ensure_evict("frag_Lsl", mlgemm_tc_lslice_bytes(nk, np));
+        lexp = (int*)h->ensure_evict("frag_Lexp", sizeof(int) * (size_t)nk * mlgemm_tc_np_pad(np));
+        if (!lsl || !lexp) return fail(h, ISDF_ERR_OOM, "device allocation of the slices of L failed");
+      } else {
+        Lwf = (float2*)h->ensure_evict("frag_Lwf", sizeof(float2) * (size_t)nk * pp);
+        if (!Lwf) return fail(h, ISDF_ERR_OOM, "device allocation of frag_Lwf failed");
+      }
       ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nf);
       ENSURE(T, float2, "frag_Tf", (size_t)nk * np * nf);
       ENSURE(M, float2, "frag_Mf", (size_t)nk * sq);
       ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
       std::vector<int2>& tl = h->tiles_host;
       herk_tc_tiles(n2, tl);
-      // B^q = w_q^{1/2} M^q L^q overwrites M^q, qc q-points at a time through Bc; the
-      // contraction then takes the B^q of S in chunks of qc q-points (fp16 slices of qc np columns).
-      const size_t per_q = herk_tc_split_bytes(n2, np);
+      // B^q = w_q^{1/2} M^q L^q overwrites M^q, qc q-points at a time (through Bc on the
+      // SIMT path); the contraction then takes the B^q of S in chunks of qc q-points
+      // (fp16 slices of qc np columns).  qc fits both slice buffers in the workspace limit.
+      const size_t per_q = std::max(herk_tc_split_bytes(n2, np), tc_ml ? mlgemm_tc_split_bytes(n2, np, 1) : 0);
       const int qc = (int)std::max<int64_t>(1, std::min<int64_t>(nS, (int64_t)(h->split_budget / per_q)));
-      ENSURE(split, uint8_t, "tc_split", herk_tc_split_bytes(n2, (int64_t)qc * np));
-      ENSURE(Bc, float2, "frag_Bc", (size_t)qc * sq);
+      ENSURE(split, uint8_t, "tc_split",
+             std::max(herk_tc_split_bytes(n2, (int64_t)qc * np), tc_ml ? mlgemm_tc_split_bytes(n2, np, qc) : 0));
+      float2* Bc = nullptr;
+      if (!tc_ml) {
+        Bc = (float2*)h->ensure_evict("frag_Bc", sizeof(float2) * (size_t)qc * sq);
+        if (!Bc) return fail(h, ISDF_ERR_OOM, "device allocation of frag_Bc failed");
+      }
       ENSURE(rexp, int, "tc_rowexp", n2);
       ENSURE(tiles_d, int2, "tc_tiles", tl.size());
       ENSURE(ws, uint8_t, "tc_ws", herk_tc_ws_bytes((int64_t)tl.size()));
       ENSURE(tcw, int, "tc_words", 4);
       CK(cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
       CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
-      if (f == 0) CK(scale_blocks_f(h->st, Lq, pp, nk, swd, Lwf));
+      if (f == 0) {
+        if (tc_ml)
+          CK(mlgemm_tc_prepare(h->st, Lq, swd, nk, np, lsl, lexp));
+        else
+          CK(scale_blocks_f(h->st, Lq, pp, nk, swd, Lwf));
+      }
       {
         StageTimer stt(h, 3, frag_m_flops(nk, np, nf, nao, km));
         CK(z2c(h->st, Cf, Cff, (int64_t)nk * nao * nf));
@@ -851,14 +875,22 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       }
       {
         StageTimer stt(h, 4, 8.0 * (double)n2 * pp * nS);
-        for (const auto& r : runs)
-          for (int q0 = r.first; q0 < r.first + r.second; q0 += qc) {
-            const int nq = std::min(qc, r.first + r.second - q0);
-            CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M + q0 * sq, np, sq, Lwf + q0 * pp, np, pp, zero, Bc,
-                     np, sq, nq));
-            CK(cudaMemcpyAsync(M + q0 * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice,
-                               h->st));
-          }
+        if (tc_ml) {
+          // row exponents of M over the q of the sum, then B^q = M^q L^q over M^q, q-chunk by q-chunk
+          CK(herk_tc_rowscale(h->st, M, sq, np, np, qmap, n2, (int64_t)nS * np, rexp));
+          for (int j0 = 0; j0 < nS; j0 += qc)
+            CK(mlgemm_tc_chunk(h->st, M, sq, qmap, n2, np, j0, std::min(qc, nS - j0), rexp, split, lsl, lexp, nk,
+                               tcw + 1));
+        } else {
+          for (const auto& r : runs)
+            for (int q0 = r.first; q0 < r.first + r.second; q0 += qc) {
+              const int nq = std::min(qc, r.first + r.second - q0);
+              CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M + q0 * sq, np, sq, Lwf + q0 * pp, np, pp, zero, Bc,
+                       np, sq, nq));
+              CK(cudaMemcpyAsync(M + q0 * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice,
+                                 h->st));
+            }
+        }
       }
       {
         StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nS * np);

@@ -431,6 +431,284 @@ __global__ void herk_finish_kernel(const float* __restrict__ wh, const float* __
   }
 }
 
+// ---------------------------------------------------------------------------
+// B^q = M^q L^q on the tensor cores with four exact slices.
+//
+// Real form: A' rows P_a = (Re M_aI, Im M_aI)_I and Q_a = interleaved(-i M_a),
+// B' rows R_J = (Re L_IJ, -Im L_IJ)_I, so (A' R_J)[P_a] = Re B_aJ and
+// (A' R_J)[Q_a] = Im B_aJ.  M rows are scaled by 2^e_a (largest component of
+// M_a over the q of the sum in [64, 128)), L columns by 2^f_qJ per q; both are
+// cut into four integer slices v = s1 + s2/128 + s3/128^2 + s4/128^3 (28 bits:
+// B = M W^T L_xi carries the cancellation of the ill-conditioned W, and three
+// slices, 21 bits, measurably degrade the traces).  Ten fp16 products feed four
+// weight groups
+//   g0 = S1T1, g1 = S1T2 + S2T1, g2 = S1T3 + S2T2 + S3T1,
+//   g3 = S1T4 + S2T3 + S3T2 + S4T1;
+// with K' = 2 N_P <= kMlMaxK every partial sum of each group is an integer of
+// magnitude below 2^24 (g3: at most 3 * 2^13 per k), so the FP32 TMEM
+// accumulation is exact; the epilogue forms g0 + g1/2^7 + g2/2^14 + g3/2^21
+// once and rescales.
+constexpr int MSL = 4;                                     // slices per operand
+constexpr int MBN = 96;                                    // output columns per tile (N of the MMA)
+constexpr int MB_BYTES = MBN * BK * 2;                     // 12 KB per slice
+constexpr int MSTAGE_BYTES = MSL * (A_BYTES + MB_BYTES);   // 112 KB
+constexpr int kMlMaxK = 640;                               // K' bound for exact accumulation
+constexpr uint32_t kIdescMl = (1u << 4) | ((uint32_t)(MBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+struct MlArgs {
+  float2* out;          // B: element (a, J) of the chunk's q-point ql at out[slot sq + a np + J]
+  const int* qmap;      // slot of the chunk's q-points (indexed j0 + ql)
+  const int* row_exp;   // e_a, [n2]
+  const int* col_exp;   // f_qJ, [Nk][np_pad] indexed by slot
+  int64_t sq;           // q stride of out
+  int n2, np, np_pad, j0, nkb;
+  int* err;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    mlgemm_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
+                     const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mA4,
+                     const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
+                     const __grid_constant__ CUtensorMap mB3, const __grid_constant__ CUtensorMap mB4, MlArgs args) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * MSTAGE_BYTES);
+  uint64_t* full = bars;               // [STAGES]
+  uint64_t* empty = bars + STAGES;     // [STAGES]
+  uint64_t* accf = bars + 2 * STAGES;  // accumulation finished
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* s_err = reinterpret_cast<volatile int*>(s_tmem + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = (2 * args.n2 + BM - 1) / BM;
+  const int ti = blockIdx.x % mt, tj = blockIdx.x / mt, ql = blockIdx.y;
+  const int slot = args.qmap ? args.qmap[args.j0 + ql] : args.j0 + ql;
+  const int nkb = args.nkb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const CUtensorMap* ma[MSL] = {&mA1, &mA2, &mA3, &mA4};
+      const CUtensorMap* mb[MSL] = {&mB1, &mB2, &mB3, &mB4};
+      const int arow = ql * 2 * args.n2 + ti * BM, brow = slot * args.np_pad + tj * MBN;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES, r = kb / STAGES;
+        if (!mbar_wait(&empty[s], (r & 1) ^ 1, s_err, args.err, 11)) break;
+        uint8_t* st = smem + s * MSTAGE_BYTES;
+        mbar_expect_tx(&full[s], MSTAGE_BYTES);
+        const int x = kb * BK;
+#pragma unroll
+        for (int i = 0; i < MSL; ++i) {
+          tma_load_2d(st + i * A_BYTES, ma[i], &full[s], x, arow);
+          tma_load_2d(st + MSL * A_BYTES + i * MB_BYTES, mb[i], &full[s], x, brow);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t g0 = tmem_base, g1 = tmem_base + MBN, g2 = tmem_base + 2 * MBN, g3 = tmem_base + 3 * MBN;
+      bool ok = true;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb % STAGES, r = kb / STAGES;
+        if (!mbar_wait(&full[s], r & 1, s_err, args.err, 12)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint8_t* st = smem + s * MSTAGE_BYTES;
+        uint64_t dA[MSL], dB[MSL];
+#pragma unroll
+        for (int i = 0; i < MSL; ++i) {
+          dA[i] = sdesc_sw128(st + i * A_BYTES);
+          dB[i] = sdesc_sw128(st + MSL * A_BYTES + i * MB_BYTES);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;
+          const uint32_t acc = (kb == 0 && kk == 0) ? 0u : 1u;
+          umma_f16(g0, dA[0] + off, dB[0] + off, kIdescMl, acc);
+          umma_f16(g1, dA[0] + off, dB[1] + off, kIdescMl, acc);
+          umma_f16(g1, dA[1] + off, dB[0] + off, kIdescMl, 1u);
+          umma_f16(g2, dA[0] + off, dB[2] + off, kIdescMl, acc);
+          umma_f16(g2, dA[1] + off, dB[1] + off, kIdescMl, 1u);
+          umma_f16(g2, dA[2] + off, dB[0] + off, kIdescMl, 1u);
+          umma_f16(g3, dA[0] + off, dB[3] + off, kIdescMl, acc);
+          umma_f16(g3, dA[1] + off, dB[2] + off, kIdescMl, 1u);
+          umma_f16(g3, dA[2] + off, dB[1] + off, kIdescMl, 1u);
+          umma_f16(g3, dA[3] + off, dB[0] + off, kIdescMl, 1u);
+        }
+        umma_commit(&empty[s]);
+      }
+      if (ok) umma_commit(accf);
+    }
+  } else {
+    // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4); rows P_a / Q_a are lanes 2i / 2i+1
+    const int q = warp & 3;
+    const int r = q * 32 + lane;            // row of the tile
+    const int64_t R = (int64_t)ti * BM + r;  // row of A'
+    const int al = r >> 1, part = r & 1;
+    const int64_t a = R >> 1;
+    // warp-uniform, so that the .sync.aligned TMEM loads are taken by whole warps
+    const bool okw = __all_sync(0xffffffffu, mbar_wait(accf, 0, s_err, args.err, 13));
+    tc_fence_after();
+    // the operand stages are idle now: stage the 64 x MBN complex tile for coalesced stores
+    constexpr int kPitch = 2 * MBN + 2;     // floats per staged row (bank-conflict padding)
+    float* tileS = reinterpret_cast<float*>(smem);
+    const int ea = (okw && a < args.n2) ? args.row_exp[a] : 0;
+    const int* fcol = args.col_exp + (int64_t)slot * args.np_pad + tj * MBN;
+#pragma unroll 1
+    for (int cb = 0; cb < MBN / 32; ++cb) {
+      uint32_t v0[32] = {}, v1[32] = {}, v2[32] = {}, v3[32] = {};
+      if (okw) {
+        const uint32_t lo = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
+        tmem_ld32(lo, v0);
+        tmem_ld32(lo + MBN, v1);
+        tmem_ld32(lo + 2 * MBN, v2);
+        tmem_ld32(lo + 3 * MBN, v3);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float v = __uint_as_float(v0[j]) +
+                        (__uint_as_float(v1[j]) * (1.0f / 128.0f) +
+                         (__uint_as_float(v2[j]) * (1.0f / 16384.0f) + __uint_as_float(v3[j]) * (1.0f / 2097152.0f)));
+        const int Jl = cb * 32 + j;
+        tileS[al * kPitch + 2 * Jl + part] = ldexpf(v, -(ea + fcol[Jl]));
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (okw) {
+      const int t = threadIdx.x - 64;
+      float2* outq = args.out + (int64_t)slot * args.sq;
+      for (int idx = t; idx < (BM / 2) * MBN; idx += 128) {
+        const int ar = idx / MBN, Jl = idx % MBN;
+        const int64_t aa = (int64_t)ti * (BM / 2) + ar;
+        const int J = tj * MBN + Jl;
+        if (aa < args.n2 && J < args.np)
+          outq[aa * args.np + J] = *reinterpret_cast<const float2*>(tileS + ar * kPitch + 2 * Jl);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ float round_int(float x) { return rintf(x); }
+__device__ __forceinline__ double round_int(double x) { return rint(x); }
+
+// Four integer slices of v (|v| < 128): v = s1 + s2/128 + s3/128^2 + s4/128^3 + r.
+template <typename R>
+__device__ __forceinline__ void slice4(R v, __half& h1, __half& h2, __half& h3, __half& h4) {
+  const R s1 = round_int(v);
+  const R r1 = (v - s1) * (R)128;
+  const R s2 = round_int(r1);
+  const R r2 = (r1 - s2) * (R)128;
+  const R s3 = round_int(r2);
+  const R r3 = (r2 - s3) * (R)128;
+  h1 = __float2half_rn((float)s1);
+  h2 = __float2half_rn((float)s2);
+  h3 = __float2half_rn((float)s3);
+  h4 = __float2half_rn((float)round_int(r3));
+}
+
+// A' slices of M for the q-points j0..j0+nq-1 of the sum: block ql holds rows
+// 2a (P_a) and 2a+1 (Q_a) over Kp columns, zero beyond 2 np.
+__global__ void msplit_kernel(BView M, int64_t n2, int np, int j0, int nq, int Kp, const int* __restrict__ row_exp,
+                              __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3,
+                              __half* __restrict__ S4) {
+  const int64_t half = Kp / 2, total = (int64_t)nq * n2 * half;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ql = e / (n2 * half), rem = e % (n2 * half);
+    const int64_t a = rem / half, k = rem % half;
+    float2 v = make_float2(0.f, 0.f);
+    if (k < np) v = M.at(a, (int64_t)(j0 + ql) * np + k);
+    const int ex = row_exp[a];
+    const float pr = ldexpf(v.x, ex), pi = ldexpf(v.y, ex);
+    const float vals[4] = {pr, pi, pi, -pr};
+    __half h1[4], h2[4], h3[4], h4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) slice4<float>(vals[t], h1[t], h2[t], h3[t], h4[t]);
+    const int64_t rP = (ql * 2 * n2 + 2 * a) * Kp + 2 * k, rQ = rP + Kp;
+    *reinterpret_cast<__half2*>(S1 + rP) = __halves2half2(h1[0], h1[1]);
+    *reinterpret_cast<__half2*>(S2 + rP) = __halves2half2(h2[0], h2[1]);
+    *reinterpret_cast<__half2*>(S3 + rP) = __halves2half2(h3[0], h3[1]);
+    *reinterpret_cast<__half2*>(S4 + rP) = __halves2half2(h4[0], h4[1]);
+    *reinterpret_cast<__half2*>(S1 + rQ) = __halves2half2(h1[2], h1[3]);
+    *reinterpret_cast<__half2*>(S2 + rQ) = __halves2half2(h2[2], h2[3]);
+    *reinterpret_cast<__half2*>(S3 + rQ) = __halves2half2(h3[2], h3[3]);
+    *reinterpret_cast<__half2*>(S4 + rQ) = __halves2half2(h4[2], h4[3]);
+  }
+}
+
+// B' slices of w_q^{1/2} L^q: block (q, J) is the row R_J = (Re L_IJ, -Im L_IJ)_I
+// scaled by 2^f_qJ (largest component in [64, 128)), rows J >= np and columns
+// beyond 2 np zero.  Layout [q][np_pad][Kp] per slice; exponents [q][np_pad].
+__global__ void lslice_kernel(const double2* __restrict__ L, const double* __restrict__ sw, int np, int np_pad,
+                              int Kp, __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3,
+                              __half* __restrict__ S4, int* __restrict__ col_exp) {
+  const int q = blockIdx.y, J = blockIdx.x;
+  const double w = sw[q];
+  const double2* Lq = L + (int64_t)q * np * np;
+  double m = 0.0;
+  if (J < np)
+    for (int I = threadIdx.x; I < np; I += blockDim.x) {
+      const double2 v = Lq[(int64_t)I * np + J];
+      m = fmax(m, fmax(fabs(v.x * w), fabs(v.y * w)));
+    }
+  __shared__ double sm[32];
+  __shared__ int s_e;
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmax(mm, sm[i]);
+    s_e = (mm > 0.0 && isfinite(mm)) ? 6 - ilogb(mm) : 0;
+    col_exp[(int64_t)q * np_pad + J] = s_e;
+  }
+  __syncthreads();
+  const int ex = s_e;
+  const int64_t row = ((int64_t)q * np_pad + J) * Kp;
+  for (int k = threadIdx.x; k < Kp / 2; k += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    if (J < np && k < np) {
+      const double2 v = Lq[(int64_t)k * np + J];
+      re = ldexp(v.x * w, ex);
+      im = -ldexp(v.y * w, ex);
+    }
+    __half a1, a2, a3, a4, b1, b2, b3, b4;
+    slice4<double>(re, a1, a2, a3, a4);
+    slice4<double>(im, b1, b2, b3, b4);
+    *reinterpret_cast<__half2*>(S1 + row + 2 * k) = __halves2half2(a1, b1);
+    *reinterpret_cast<__half2*>(S2 + row + 2 * k) = __halves2half2(a2, b2);
+    *reinterpret_cast<__half2*>(S3 + row + 2 * k) = __halves2half2(a3, b3);
+    *reinterpret_cast<__half2*>(S4 + row + 2 * k) = __halves2half2(a4, b4);
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -550,6 +828,59 @@ cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int
   e = herk_tc_chunk(st, B, 0, ldb, K, nullptr, n2, 0, K, row_exp, split, tiles_d, ntiles, ws, 0, err);
   if (e != cudaSuccess) return e;
   return herk_tc_finish(st, ws, tiles_d, ntiles, n2, row_exp, scale, E);
+}
+
+// ---- B = M L on the tensor cores, four slices (host side)
+int mlgemm_tc_kp(int np) { return ((2 * np + tc::BK - 1) / tc::BK) * tc::BK; }
+int mlgemm_tc_np_pad(int np) { return ((np + tc::MBN - 1) / tc::MBN) * tc::MBN; }
+bool mlgemm_tc_supported(int np) { return np > 0 && mlgemm_tc_kp(np) <= tc::kMlMaxK; }
+size_t mlgemm_tc_lslice_bytes(int nk, int np) {
+  return (size_t)tc::MSL * nk * mlgemm_tc_np_pad(np) * mlgemm_tc_kp(np) * sizeof(__half) + 256;
+}
+size_t mlgemm_tc_split_bytes(int64_t n2, int np, int nq) {
+  return (size_t)tc::MSL * nq * (2 * n2) * mlgemm_tc_kp(np) * sizeof(__half) + 256;
+}
+
+cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, void* lsl,
+                              int* col_exp) {
+  using namespace tc;
+  const int Kp = mlgemm_tc_kp(np), npp = mlgemm_tc_np_pad(np);
+  const size_t per = (size_t)nk * npp * Kp;
+  __half* S1 = reinterpret_cast<__half*>(lsl);
+  lslice_kernel<<<dim3(npp, nk), 128, 0, st>>>(L, sw, np, npp, Kp, S1, S1 + per, S1 + 2 * per, S1 + 3 * per,
+                                                col_exp);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* qmap, int64_t n2, int np, int j0,
+                            int nq, const int* row_exp, void* split, const void* lsl, const int* col_exp, int nk,
+                            int* err) {
+  using namespace tc;
+  if (n2 <= 0 || nq <= 0) return cudaSuccess;
+  if (!mlgemm_tc_supported(np)) return cudaErrorInvalidValue;
+  const int Kp = mlgemm_tc_kp(np), npp = mlgemm_tc_np_pad(np);
+  const size_t pa = (size_t)nq * (2 * n2) * Kp, pb = (size_t)nk * npp * Kp;
+  __half* S1 = reinterpret_cast<__half*>(split);
+  BView mv{M, sq, np, np, qmap};
+  msplit_kernel<<<nblk((int64_t)nq * n2 * (Kp / 2)), 256, 0, st>>>(mv, n2, np, j0, nq, Kp, row_exp, S1, S1 + pa,
+                                                                   S1 + 2 * pa, S1 + 3 * pa);
+  count_launch();
+  const __half* L1 = reinterpret_cast<const __half*>(lsl);
+  CUtensorMap mA[MSL], mB[MSL];
+  for (int i = 0; i < MSL; ++i)
+    if (!make_map(&mA[i], S1 + i * pa, Kp, (int64_t)nq * 2 * n2, Kp, BM) ||
+        !make_map(&mB[i], L1 + i * pb, Kp, (int64_t)nk * npp, Kp, MBN))
+      return cudaErrorInvalidValue;
+  const size_t smem = (size_t)STAGES * MSTAGE_BYTES + 1024 + 256;
+  cudaError_t e = cudaFuncSetAttribute(mlgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int mt = (int)((2 * n2 + BM - 1) / BM), ntj = npp / MBN;
+  MlArgs args{M, qmap, row_exp, col_exp, sq, (int)n2, np, npp, j0, Kp / BK, err};
+  mlgemm_tc_kernel<<<dim3(mt * ntj, nq), NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mA[3], mB[0], mB[1], mB[2],
+                                                                mB[3], args);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace isdf
