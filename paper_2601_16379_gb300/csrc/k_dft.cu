@@ -465,24 +465,64 @@ cudaError_t grid_fft_launch(cudaStream_t st, T* x, int rows_per_q, int q0, int n
   return cudaGetLastError();
 }
 
+// Z[R][(p q)][I] = conj(t[R][I][p]) t[R][I][q].  Block (p-tile of kPairP, R):
+// tiles of kPairQ columns q of t[R] go through shared memory with coalesced
+// loads (row pitch kPairQ + 1 against bank conflicts), and the outputs are
+// written with consecutive I across threads.  Each block reads the slab t[R]
+// once per p-tile from L2 and writes kPairP n_f n_p values.
+constexpr int kPairP = 4, kPairQ = 16;
+
 template <typename T>
-__global__ void pair_kernel(const T* __restrict__ t, int nk, int np, int nf, T* __restrict__ Z) {
-  const int64_t per = (int64_t)nf * nf * np;
-  const int64_t total = per * nk;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int I = (int)(e % np);
-    const int64_t pq = (e / np) % ((int64_t)nf * nf);
-    const int R = (int)(e / per);
-    const int p = (int)(pq / nf), q = (int)(pq % nf);
-    const T* tr = t + (int64_t)R * np * nf + (int64_t)I * nf;
-    const T a = tr[p], b = tr[q];
-    // conj(a) * b
-    T z;
-    z.x = a.x * b.x + a.y * b.y;
-    z.y = a.x * b.y - a.y * b.x;
-    Z[e] = z;
+__global__ void __launch_bounds__(256) pair_kernel(const T* __restrict__ t, int np, int nf, T* __restrict__ Z) {
+  extern __shared__ __align__(16) unsigned char pair_smem[];
+  T* ts = reinterpret_cast<T*>(pair_smem);  // [np][kPairQ + 1]
+  const int R = blockIdx.y, p0 = blockIdx.x * kPairP;
+  const T* tr = t + (int64_t)R * np * nf;
+  T* zr = Z + (int64_t)R * nf * nf * np;
+  for (int q0 = 0; q0 < nf; q0 += kPairQ) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * kPairQ; e += blockDim.x) {
+      const int I = e / kPairQ, j = e % kPairQ, q = q0 + j;
+      T v;
+      v.x = 0;
+      v.y = 0;
+      if (q < nf) v = tr[(int64_t)I * nf + q];
+      ts[I * (kPairQ + 1) + j] = v;
+    }
+    __syncthreads();
+    const int nq = min(kPairQ, nf - q0);
+    for (int I = threadIdx.x; I < np; I += blockDim.x) {
+#pragma unroll
+      for (int pi = 0; pi < kPairP; ++pi) {
+        const int p = p0 + pi;
+        if (p >= nf) break;
+        const T a = tr[(int64_t)I * nf + p];
+        T* zp = zr + ((int64_t)p * nf + q0) * np + I;
+        for (int j = 0; j < nq; ++j) {
+          const T b = ts[I * (kPairQ + 1) + j];
+          T z;
+          z.x = a.x * b.x + a.y * b.y;  // conj(a) b
+          z.y = a.x * b.y - a.y * b.x;
+          zp[(int64_t)j * np] = z;
+        }
+      }
+    }
   }
+}
+
+template <typename T>
+cudaError_t pair_launch(cudaStream_t st, const T* t, int nk, int np, int nf, T* Z) {
+  if ((int64_t)nk * nf * np == 0) return cudaSuccess;
+  if (nk > 65535) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)np * (kPairQ + 1) * sizeof(T);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  pair_kernel<T><<<dim3((nf + kPairP - 1) / kPairP, nk), 256, smem, st>>>(t, np, nf, Z);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -515,22 +555,10 @@ void grid_twiddles(const int mesh[3], double2* host192) {
     }
 }
 cudaError_t pair_products(cudaStream_t st, const double2* t, int nk, int np, int nf, double2* Z) {
-  const int64_t total = (int64_t)nk * nf * nf * np;
-  int nb = (int)((total + 255) / 256);
-  if (nb > 152 * 64) nb = 152 * 64;
-  if (total == 0) return cudaSuccess;
-  pair_kernel<double2><<<nb, 256, 0, st>>>(t, nk, np, nf, Z);
-  count_launch();
-  return cudaGetLastError();
+  return pair_launch<double2>(st, t, nk, np, nf, Z);
 }
 cudaError_t pair_products_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float2* Z) {
-  const int64_t total = (int64_t)nk * nf * nf * np;
-  int nb = (int)((total + 255) / 256);
-  if (nb > 152 * 64) nb = 152 * 64;
-  if (total == 0) return cudaSuccess;
-  pair_kernel<float2><<<nb, 256, 0, st>>>(t, nk, np, nf, Z);
-  count_launch();
-  return cudaGetLastError();
+  return pair_launch<float2>(st, t, nk, np, nf, Z);
 }
 
 }  // namespace isdf
