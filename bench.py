@@ -117,6 +117,16 @@ def profile_traffic(kernel_file: str, workload: str):
     return float(t.group(1))
 
 
+def reduce_max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks (the job is as
+    slow as its slowest replica); identity without a process group."""
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 # ------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -202,10 +212,7 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
-    t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = reduce_max_over_ranks([ms, e2e_ms], dist, "cuda")
 
     peaks, peak_src = measured_peaks()
     if prec == B.ISDF_MIXED:
