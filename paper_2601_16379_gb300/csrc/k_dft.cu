@@ -177,9 +177,7 @@ cudaError_t kdft_cubic_launch(cudaStream_t st, T* data, int64_t ncol, int mode, 
                               const Twiddles16& t2, double scale) {
   constexpr int nk = L * L * L;
   int lct = 0;
-  // columns per block: at most 32 KB of shared memory, so that ~7 blocks share an SM and
-  // hide the latency of the strided column loads
-  while (lct < 5 && ((int64_t)nk * sizeof(T) << (lct + 1)) <= 32768) ++lct;
+  while (lct < 5 && ((int64_t)nk * sizeof(T) << (lct + 1)) <= 65536) ++lct;
   const size_t smem = (size_t)nk * sizeof(T) << lct;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kdft_cubic_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
