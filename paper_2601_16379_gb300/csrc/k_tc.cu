@@ -1,5 +1,7 @@
-// Tensor-core (tcgen05) contraction of the fragment ERIs, Eq. 19:
+// Tensor-core (tcgen05) kernels of the fragment ERIs, Eq. 19:
 //     E = sum_q B^q B^q^H   with  B^q = M^q L^q   (V^q = L^q L^q^H).
+// herk_tc_kernel forms E (below); mlgemm_tc_kernel forms B (further down, with
+// four slices instead of three).
 //
 // Complex -> real: with B stored as interleaved (re, im) pairs, the real row
 // P_a = (Re B_a0, Im B_a0, Re B_a1, ...) and Q_a = interleaved(-i B_a) give
