@@ -1,4 +1,6 @@
-"""Full-size checks at the c4 workload (Nk = 216, 24^3 grid, N_P = 300), in the
+"""Full-size checks at the c3 and c4 workloads (c4 first; c3 at the end).
+
+c4: (Nk = 216, 24^3 grid, N_P = 300), in the
 launch configuration that bench.py times (mixed precision, tensor-core
 contraction, all steps).
 
@@ -104,3 +106,41 @@ def test_properties_at_full_size(c4_runs):
             hyy = np.array([e[dd_, cc, cc, dd_] for cc, dd_ in zip(c, dd)]).real
             assert np.all(np.abs(hxy) ** 2 <= hxx * hyy * (1 + 1e-6) + tol * s * s)
             assert out[prec]["ej"][i] > 0 > out[prec]["ek"][i]
+
+
+@pytest.fixture(scope="module")
+def c3_runs(cuda, lib_built):
+    """c3 at its own size (52 AOs, 4x4x4 mesh, 32^3 grid, N_P = 500, 3 fragments of 60):
+    N_P = 500 puts B = M L on the compensated SIMT GEMM in the mixed path."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl = W.workload("c3")
+    out = {}
+    for prec in (B.ISDF_MIXED, B.ISDF_FP64):
+        g = B.Isdf(wl.cell, prec)
+        g.build_points(wl.n_p, wl.seed)
+        g.fit_zeta(TAU)
+        g.coulomb_metric()
+        dt = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
+        Cs = [torch.from_numpy(f.C).cuda() for f in wl.fragments]
+        gs = [torch.from_numpy(f.gamma).cuda() for f in wl.fragments]
+        eris = [torch.empty((f.norb,) * 4, dtype=dt, device="cuda") for f in wl.fragments]
+        ej, ek = g.fragment_eri(Cs, gs, eris)
+        torch.cuda.synchronize()
+        out[prec] = dict(eri=[e.cpu().numpy().astype(np.complex128) for e in eris], ej=ej, ek=ek)
+        g.close()
+    return wl, out
+
+
+def test_c3_mixed_matches_fp64_and_symmetries(c3_runs):
+    from paper_2601_16379_gb300 import binding as B
+    wl, out = c3_runs
+    m, d = out[B.ISDF_MIXED], out[B.ISDF_FP64]
+    for i, f in enumerate(wl.fragments):
+        assert np.abs(m["eri"][i] - d["eri"][i]).max() < MIXED_TOL
+        assert abs(m["ej"][i] - d["ej"][i]) < MIXED_TOL and abs(m["ek"][i] - d["ek"][i]) < MIXED_TOL
+        e = d["eri"][i]
+        s = np.abs(e).max()
+        assert np.abs(e - e.transpose(2, 3, 0, 1)).max() < 1e-10 * s       # (pq|rs) = (rs|pq)
+        assert np.abs(e - e.transpose(1, 0, 3, 2).conj()).max() < 1e-10 * s  # = conj((qp|sr))
+        assert d["ej"][i] > 0 > d["ek"][i]
