@@ -1,6 +1,5 @@
-"""Full-size checks at the c3 and c4 workloads (c4 first; c3 at the end).
-
-c4: (Nk = 216, 24^3 grid, N_P = 300), in the
+"""Full-size checks at the c4 workload (Nk = 216, 24^3 grid, N_P = 300) and,
+at the end of the file, at c3 (52 AOs, Nk = 64, 32^3 grid, N_P = 500). c4 runs in the
 launch configuration that bench.py times (mixed precision, tensor-core
 contraction, all steps).
 
