@@ -59,7 +59,7 @@ __all__ = [
     "coulomb_metric", "fragment_T", "pair_tensor", "fragment_E", "eri_from_E",
     "fragment_eri", "traces", "cheap_J", "run_isdf", "fftdf_fragment_eri",
     "supercell", "supercell_coefficients", "supercell_ips", "TIE_EPS", "LATTICE_EXP_CUT",
-    "pinv_pchol", "coulomb_metric_eta", "exchange_matrix", "fftdf_exchange_matrix",
+    "pinv_pchol", "coulomb_metric_eta", "exchange_matrix", "fftdf_exchange_matrix", "ao_eri",
 ]
 
 # exp(-40) tail rule of the lattice sum (Eq. 1): images whose Gaussian factor
@@ -495,6 +495,33 @@ def cheap_J(M: np.ndarray, V: np.ndarray, gamma: np.ndarray, nk: int) -> float:
         a = g @ M[i]
         tot += a @ V[i] @ a.conj()
     return float((tot / (2.0 * nk)).real)
+
+
+# ----------------------------------------------------------------------------
+# AO-level integrals for arbitrary k-quartets (Eq. 9)
+# ----------------------------------------------------------------------------
+
+def ao_eri(X: np.ndarray, V: np.ndarray, quartets: Sequence[Sequence[int]], kmesh: Sequence[int]) -> np.ndarray:
+    """(mu k1 nu k2 | lam k3 sig k4) of the Bloch AOs Phi^k / sqrt(Nk) (normalised
+    over the Nk-cell supercell), chemist's order, from the ISDF factors (Eq. 9):
+
+      Nk sum_IJ conj(X^{k1}_{I mu}) X^{k2}_{I nu} V^{Q}_{IJ} conj(X^{k3}_{J lam}) X^{k4}_{J sig},
+      Q = k1 - k2, which must equal k4 - k3 (crystal momentum; other quartets vanish).
+
+    Written directly from the definition of the fragment ERIs for orbitals that are
+    single Bloch AOs.  Returns (n_quartets, N_AO, N_AO, N_AO, N_AO)."""
+    nk = X.shape[0]
+    km = k_minus_table(kmesh)
+    kp = k_plus_table(kmesh)
+    out = []
+    for k1, k2, k3, k4 in quartets:
+        Q = km[k1, k2]                      # k1 - k2
+        if kp[k3, Q] != k4:                 # k4 = k3 + Q
+            raise ValueError("quartet does not conserve crystal momentum")
+        A = np.einsum("im,in->imn", X[k1].conj(), X[k2])     # (N_P, mu, nu)
+        Cc = np.einsum("jl,js->jls", X[k3].conj(), X[k4])    # (N_P, lam, sig)
+        out.append(nk * np.einsum("imn,ij,jls->mnls", A, V[Q], Cc))
+    return np.array(out)
 
 
 # ----------------------------------------------------------------------------

@@ -319,6 +319,62 @@ def test_time_reversal_half_sum(kmesh):
     assert np.abs(E2 - E).max() < 1e-10 * np.abs(E).max()
 
 
+def _single_ao_orbitals(cell, ks):
+    """C selecting every Bloch AO at each k of ks, normalised over the supercell:
+    orbital (i, mu) is Phi^{ks[i]}_mu / sqrt(Nk)."""
+    nk, nao = cell.nkpts, cell.nao
+    C = np.zeros((nk, nao, len(ks) * nao), np.complex128)
+    for i, k in enumerate(ks):
+        C[k, :, i * nao:(i + 1) * nao] = math.sqrt(nk) * np.eye(nao)
+    return C
+
+
+def test_ao_quartet_eri_equals_single_ao_fragments(tiny5):
+    """Eq. 9: the AO integrals of a k-quartet equal the fragment ERIs whose orbitals
+    are those Bloch AOs (an independent route through the pair tensor, Eq. 20)."""
+    cell, phi, ips, nf = tiny5
+    r = O.run_isdf(cell, 12, 7, solve_tol=1e-14, ips=ips[:12], phi=phi)
+    kp, km = O.k_plus_table(cell.kmesh), O.k_minus_table(cell.kmesh)
+    nao = cell.nao
+    quartets = [(0, 0, 0, 0), (1, 4, 2, kp[2, km[1, 4]]), (5, 13, 26, kp[26, km[5, 13]])]
+    ao = O.ao_eri(r["X"], r["V"], quartets, cell.kmesh)
+    s = np.abs(ao).max()
+    for n, qt in enumerate(quartets):
+        C = _single_ao_orbitals(cell, qt)
+        frag = O.fragment_eri(r["X"], r["V"], C, cell.kmesh)
+        assert np.abs(frag[0:nao, nao:2 * nao, 2 * nao:3 * nao, 3 * nao:] - ao[n]).max() < 1e-11 * s
+
+
+def test_ao_quartet_eri_exact_limit(tiny):
+    """At the pair-space rank the AO k-quartet integrals equal the grid-exact
+    (FFTDF) integrals of the same Bloch AOs."""
+    cell, phi, ips, nf = tiny
+    r = O.run_isdf(cell, nf, 7, solve_tol=1e-14, ips=ips[:nf], phi=phi)
+    kp, km = O.k_plus_table(cell.kmesh), O.k_minus_table(cell.kmesh)
+    nao = cell.nao
+    for qt in [(0, 0, 0, 0), (1, 6, 3, kp[3, km[1, 6]]), (7, 2, 5, kp[5, km[7, 2]])]:
+        ao = O.ao_eri(r["X"], r["V"], [qt], cell.kmesh)[0]
+        grid = O.fftdf_fragment_eri(cell, _single_ao_orbitals(cell, qt))[0:nao, nao:2 * nao, 2 * nao:3 * nao, 3 * nao:]
+        assert np.abs(grid - ao).max() < 1e-9 * np.abs(grid).max()
+
+
+def test_ao_quartet_symmetries_and_momentum(tiny5):
+    """(mu k1 nu k2|lam k3 sig k4) = (lam k3 sig k4|mu k1 nu k2) = conj(nu k2 mu k1|sig k4 lam k3);
+    quartets that do not conserve crystal momentum are refused."""
+    cell, phi, ips, nf = tiny5
+    r = O.run_isdf(cell, 12, 7, solve_tol=1e-8, ips=ips[:12], phi=phi)
+    kp, km = O.k_plus_table(cell.kmesh), O.k_minus_table(cell.kmesh)
+    k1, k2, k3 = 3, 11, 20
+    k4 = kp[k3, km[k1, k2]]
+    a, b, c = O.ao_eri(r["X"], r["V"], [(k1, k2, k3, k4), (k3, k4, k1, k2), (k2, k1, k4, k3)], cell.kmesh)
+    s = np.abs(a).max()
+    # V^{-q} = conj(V^q) and V^q Hermitian, each up to the fit's rounding
+    assert np.abs(a - b.transpose(2, 3, 0, 1)).max() < 1e-11 * s
+    assert np.abs(a - c.transpose(1, 0, 3, 2).conj()).max() < 1e-11 * s
+    with pytest.raises(ValueError):
+        O.ao_eri(r["X"], r["V"], [(k1, k2, k3, kp[k4, 1])], cell.kmesh)
+
+
 def test_eri_symmetries(c1run):
     wl, r = c1run
     f = W.make_fragment(wl.cell, wl.seed, 3, 5)
