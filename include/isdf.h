@@ -172,6 +172,22 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb,
  * Needs the Coulomb metric (either route). */
 int isdf_exchange(isdf_handle* h, const void* P, void* K_out);
 
+/* Two-electron integrals of Bloch AOs for arbitrary k-quartets in the THC form
+ * of Eq. 9, FP64, chemist's order:
+ *   (mu k1 nu k2 | lam k3 sig k4)
+ *     = Nk sum_IJ conj(X^{k1}_{I mu}) X^{k2}_{I nu} V^{Q}_{IJ} conj(X^{k3}_{J lam}) X^{k4}_{J sig},
+ *   Q = k1 - k2,
+ * for the Bloch AOs Phi^k_mu / sqrt(Nk) normalised over the Nk-cell supercell
+ * (the fragment ERIs of isdf_fragment_eri for orbitals that are single Bloch
+ * AOs).  The conjugates place the paper's X^{-k} = conj(X^k) on the first index
+ * of each pair.
+ *   quartets  host int32 [n_quartet][4]: flat k indices (k1, k2, k3, k4); every
+ *             quartet must conserve crystal momentum, k1 - k2 = k4 - k3 on the
+ *             mesh (other quartets vanish), else ISDF_ERR_ARG
+ *   out       device complex128 [n_quartet][N_AO][N_AO][N_AO][N_AO]
+ * Needs the Coulomb metric (either route). */
+int isdf_ao_eri(isdf_handle* h, int n_quartet, const int32_t* quartets, void* out);
+
 /* Time-reversal pairing (default on).  The AO basis is real and the k-mesh
  * Gamma-centred, so Pi^{-q} = conj(Pi^q) and eta^{-q} = conj(eta^q) (Eqs. 4-5),
  * hence zeta^{-q} = conj(zeta^q) and V^{-q} = conj(V^q); and for any orbitals

@@ -25,6 +25,7 @@ STATUS = {0: "ISDF_OK", -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_OOM", -3: "ISDF_ERR_CU
 # Every entry point declared in include/isdf.h.
 EXPORTS = ["isdf_create", "isdf_build_points", "isdf_set_points", "isdf_fit_zeta",
            "isdf_coulomb_metric", "isdf_coulomb_metric_eta", "isdf_fragment_eri", "isdf_exchange",
+           "isdf_ao_eri",
            "isdf_set_time_reversal", "isdf_set_workspace_limit", "isdf_get", "isdf_sizes",
            "isdf_launch_count", "isdf_timing_enable", "isdf_timing_get", "isdf_eri_traces_noalloc",
            "isdf_last_error", "isdf_destroy"]
@@ -65,6 +66,7 @@ def load(path: Optional[str] = None) -> ct.CDLL:
     lib.isdf_coulomb_metric_eta.argtypes = [vp, vp]
     lib.isdf_fragment_eri.argtypes = [vp, ct.c_int, i32p, ct.POINTER(vp), ct.POINTER(vp), ct.POINTER(vp), dp, dp]
     lib.isdf_exchange.argtypes = [vp, vp, vp]
+    lib.isdf_ao_eri.argtypes = [vp, ct.c_int, i32p, vp]
     lib.isdf_set_time_reversal.argtypes = [vp, ct.c_int]
     lib.isdf_set_workspace_limit.argtypes = [vp, ct.c_uint64]
     lib.isdf_get.argtypes = [vp, ct.c_int, vp]
@@ -216,6 +218,13 @@ class Isdf:
         """k-point exchange matrix K^k (Eq. 10) for the AO density matrices P^k."""
         self._check(self.lib.isdf_exchange(self.h, _ptr(P), _ptr(K_out)))
         return K_out
+
+    def ao_eri(self, quartets, out):
+        """AO-level integrals (mu k1 nu k2|lam k3 sig k4) for k-quartets (Eq. 9), FP64."""
+        q = np.ascontiguousarray(np.asarray(quartets, np.int32).reshape(-1, 4))
+        self._check(self.lib.isdf_ao_eri(self.h, int(q.shape[0]), q.ctypes.data_as(ct.POINTER(ct.c_int32)),
+                                         _ptr(out)))
+        return out
 
     def get(self, what: int, out):
         self._check(self.lib.isdf_get(self.h, int(what), _ptr(out)))

@@ -188,6 +188,8 @@ cudaError_t eri_swapconj_sym(cudaStream_t st, double2* E, int nf);
 // out[b] = sw[b] L[b] over nb blocks of `per` elements (FP64 / to complex64).
 cudaError_t scale_blocks(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, double2* out);
 cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, float2* out);
+// out[I][mu n_ao + nu] = conj(x1[I][mu]) x2[I][nu] for I < np (x1, x2: [np][n_ao]).
+cudaError_t ao_pairs(cudaStream_t st, const double2* x1, const double2* x2, int np, int nao, double2* out);
 // x[pairs[i].x] = conj(x[pairs[i].y]) for blocks of `per` elements.
 cudaError_t mirror_conj(cudaStream_t st, double2* x, int64_t per, const int2* pairs, int npairs);
 // out[b][I][J] = a[b][J][I] * c[b][I][J] for nb blocks of n x n.

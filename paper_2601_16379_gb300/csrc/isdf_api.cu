@@ -926,6 +926,61 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
   return ISDF_OK;
 }
 
+int isdf_ao_eri(isdf_handle* h, int n_quartet, const int32_t* quartets, void* out) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!h->has_coulomb) return fail(h, ISDF_ERR_STATE, "isdf_ao_eri before the Coulomb metric");
+  if (n_quartet < 0 || (n_quartet > 0 && (!quartets || !out))) return fail(h, ISDF_ERR_ARG, "invalid quartet arrays");
+  const int nk = h->nk, np = h->np, nao = h->nao;
+  const int* km = h->cell.kmesh;
+  auto coords = [&](int k, int m[3]) {
+    m[0] = k / (km[1] * km[2]);
+    m[1] = (k / km[2]) % km[1];
+    m[2] = k % km[2];
+  };
+  auto flat = [&](const int m[3]) {
+    return ((((m[0] % km[0]) + km[0]) % km[0]) * km[1] + (((m[1] % km[1]) + km[1]) % km[1])) * km[2] +
+           (((m[2] % km[2]) + km[2]) % km[2]);
+  };
+  std::vector<int> qv(n_quartet);
+  for (int n = 0; n < n_quartet; ++n) {
+    const int32_t* k = quartets + 4 * n;
+    for (int i = 0; i < 4; ++i)
+      if (k[i] < 0 || k[i] >= nk) return fail(h, ISDF_ERR_ARG, "quartet %d: k index out of range", n);
+    int m1[3], m2[3], m3[3], m4[3], d[3], s4[3];
+    coords(k[0], m1), coords(k[1], m2), coords(k[2], m3), coords(k[3], m4);
+    for (int a = 0; a < 3; ++a) {
+      d[a] = m1[a] - m2[a];
+      s4[a] = m3[a] + d[a];
+    }
+    if (flat(s4) != k[3])
+      return fail(h, ISDF_ERR_ARG, "quartet %d does not conserve crystal momentum (k1 - k2 != k4 - k3)", n);
+    qv[n] = flat(d);
+  }
+  const int64_t nao2 = (int64_t)nao * nao, pp = (int64_t)np * np, pa = (int64_t)np * nao;
+  double2* X = (double2*)h->buf("X");
+  double2* Lq = (double2*)h->buf("Lq");
+  ENSURE(A, double2, "ao_pairs_a", (size_t)np * nao2);
+  ENSURE(Cc, double2, "ao_pairs_c", (size_t)np * nao2);
+  ENSURE(U, double2, "ao_u", (size_t)np * nao2);
+  ENSURE(Wm, double2, "ao_w", (size_t)np * nao2);
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  for (int n = 0; n < n_quartet; ++n) {
+    const int32_t* k = quartets + 4 * n;
+    const double2* L = Lq + qv[n] * pp;
+    CK(ao_pairs(h->st, X + k[0] * pa, X + k[1] * pa, np, nao, A));
+    CK(ao_pairs(h->st, X + k[2] * pa, X + k[3] * pa, np, nao, Cc));
+    // (mu nu|lam sig) = Nk A^T V^Q C with V^Q = L L^H: (L^T A)^T (L^H C)
+    CK(zgemm(h->st, 'T', 'N', np, (int)nao2, np, one, L, np, 0, A, nao2, 0, zero, U, nao2, 0, 1));
+    CK(zgemm(h->st, 'C', 'N', np, (int)nao2, np, one, L, np, 0, Cc, nao2, 0, zero, Wm, nao2, 0, 1));
+    CK(zgemm(h->st, 'T', 'N', (int)nao2, (int)nao2, np, make_double2((double)nk, 0.0), U, nao2, 0, Wm, nao2, 0,
+             zero, (double2*)out + (int64_t)n * nao2 * nao2, nao2, 0, 1));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return ISDF_OK;
+}
+
 int isdf_exchange(isdf_handle* h, const void* P, void* K_out) {
   if (!h || !P || !K_out) return fail(h, ISDF_ERR_ARG, "isdf_exchange: NULL argument");
   LaunchScope ls(h);

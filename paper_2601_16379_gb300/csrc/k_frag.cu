@@ -159,6 +159,18 @@ __global__ void mirror_kernel(T* __restrict__ x, int64_t per, const int2* __rest
   }
 }
 
+// out[I][mu n_ao + nu] = conj(x1[I][mu]) x2[I][nu]  (AO pair rows of one k-pair)
+__global__ void ao_pair_kernel(const double2* __restrict__ x1, const double2* __restrict__ x2, int np, int nao,
+                               double2* __restrict__ out) {
+  const int64_t n2 = (int64_t)nao * nao, total = (int64_t)np * n2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = e / n2;
+    const int mu = (int)((e % n2) / nao), nu = (int)(e % nao);
+    const double2 a = x1[I * nao + mu], b = x2[I * nao + nu];
+    out[e] = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+  }
+}
+
 __global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = make_float2((float)in[e].x, (float)in[e].y);
@@ -232,6 +244,12 @@ cudaError_t scale_blocks(cudaStream_t st, const double2* L, int64_t per, int nb,
 }
 cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, float2* out) {
   scale_blocks_kernel<float2><<<nblocks(per * nb), 256, 0, st>>>(L, per, nb, sw, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t ao_pairs(cudaStream_t st, const double2* x1, const double2* x2, int np, int nao, double2* out) {
+  ao_pair_kernel<<<nblocks((int64_t)np * nao * nao), 256, 0, st>>>(x1, x2, np, nao, out);
   count_launch();
   return cudaGetLastError();
 }

@@ -299,6 +299,42 @@ def test_eri_out_in_pinned_host_memory(cuda, lib_built, c1, prec):
     g.close()
 
 
+@pytest.mark.parametrize("case", ["c1", "aniso"])
+def test_ao_quartet_eri_matches_oracle(cuda, lib_built, c1, aniso, case):
+    """AO-level integrals for k-quartets (Eq. 9) against the oracle, including
+    quartets whose Q lies in the conjugated half of the mesh; a quartet that does
+    not conserve crystal momentum is refused."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    if case == "c1":
+        wl, o = c1
+        cell = wl.cell
+    else:
+        cell, o = aniso
+    tol = 1e-7
+    _, _, V = o.fit(tol)
+    kp, km = O.k_plus_table(cell.kmesh), O.k_minus_table(cell.kmesh)
+    nk = cell.nkpts
+    quartets = [(0, 0, 0, 0), (1, 0, 0, kp[0, 1]), (nk - 1, 2 % nk, 3 % nk, kp[3 % nk, km[nk - 1, 2 % nk]]),
+                (2 % nk, nk - 1, 4 % nk, kp[4 % nk, km[2 % nk, nk - 1]])]
+    ref = O.ao_eri(o.X, V, quartets, cell.kmesh)
+    g = B.Isdf(cell, B.ISDF_FP64)
+    g.set_points(o.ips)
+    g.fit_zeta(tol)
+    g.coulomb_metric()
+    nao = cell.nao
+    out = torch.empty((len(quartets), nao, nao, nao, nao), dtype=torch.complex128, device="cuda")
+    g.ao_eri(quartets, out)
+    got = out.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    bad = [(1, 0, 0, 0)] if nk > 1 else None
+    if bad:
+        with pytest.raises(B.IsdfError) as e:
+            g.ao_eri(bad, torch.empty((1, nao, nao, nao, nao), dtype=torch.complex128, device="cuda"))
+        assert e.value.code == -1
+    g.close()
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7)])
 def test_eri_c2(cuda, lib_built, c2, prec, tol):
     from paper_2601_16379_gb300 import binding as B
