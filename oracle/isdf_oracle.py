@@ -60,6 +60,7 @@ __all__ = [
     "fragment_eri", "traces", "cheap_J", "run_isdf", "fftdf_fragment_eri",
     "supercell", "supercell_coefficients", "supercell_ips", "TIE_EPS", "LATTICE_EXP_CUT",
     "pinv_pchol", "coulomb_metric_eta", "exchange_matrix", "fftdf_exchange_matrix", "ao_eri",
+    "green_ip", "polarizability", "sos_trace",
 ]
 
 # exp(-40) tail rule of the lattice sum (Eq. 1): images whose Gaussian factor
@@ -522,6 +523,54 @@ def ao_eri(X: np.ndarray, V: np.ndarray, quartets: Sequence[Sequence[int]], kmes
         Cc = np.einsum("jl,js->jls", X[k3].conj(), X[k4])    # (N_P, lam, sig)
         out.append(nk * np.einsum("imn,ij,jls->mnls", A, V[Q], Cc))
     return np.array(out)
+
+
+# ----------------------------------------------------------------------------
+# k-SOS-MP2 polarisability in the interpolation-point basis (Eqs. 11-15)
+# ----------------------------------------------------------------------------
+
+def green_ip(X: np.ndarray, C: np.ndarray, eps: np.ndarray, n_occ: int, tau: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Imaginary-time Green's functions of the occupied and the virtual orbitals at
+    the interpolation points, for tau >= 0 (Eq. 15 with decaying exponentials):
+
+      Go^k_{IJ}(tau) = sum_{i occ} Y^k_{Ii} conj(Y^k_{Ji}) exp(+tau eps^k_i),
+      Gv^k_{IJ}(tau) = sum_{a vir} Y^k_{Ia} conj(Y^k_{Ja}) exp(-tau eps^k_a),
+      Y^k = X^k C^k  (orbital values at the points, Eq. 14),
+
+    with energies measured from a chemical potential inside the gap."""
+    Y = np.einsum("kim,kmn->kin", X, C)
+    wo = np.exp(tau * eps[:, :n_occ])
+    wv = np.exp(-tau * eps[:, n_occ:])
+    Go = np.einsum("kin,kn,kjn->kij", Y[:, :, :n_occ], wo, Y[:, :, :n_occ].conj())
+    Gv = np.einsum("kia,ka,kja->kij", Y[:, :, n_occ:], wv, Y[:, :, n_occ:].conj())
+    return Go, Gv
+
+
+def polarizability(Go: np.ndarray, Gv: np.ndarray, kmesh: Sequence[int]) -> np.ndarray:
+    """chi^Q_{IK}(tau) = sum_k Go^k_{KI}(tau) Gv^{k-Q}_{IK}(tau)  (Eq. 13 before the
+    kernel: the element-wise k-convolution of the two Green's functions), by the
+    direct k-sum.  chi^Q is Hermitian positive semidefinite."""
+    km = k_minus_table(kmesh)
+    nk = Go.shape[0]
+    out = np.zeros_like(Go)
+    for Q in range(nk):
+        for k in range(nk):
+            out[Q] += Go[k].T * Gv[km[k, Q]]
+    return out
+
+
+def sos_trace(chi: np.ndarray, V: np.ndarray, kmesh: Sequence[int]) -> float:
+    """S(tau) = Nk^2 sum_Q tr[conj(V^Q) chi^Q conj(V^Q) (chi^{-Q})^T] = sum_{ia,jb}
+    |(ia|jb)|^2 exp(-tau (eps_a - eps_i + eps_b - eps_j)) over the orbitals of the
+    Nk-cell supercell (Eq. 12 with P^Q = chi^Q V^Q).  The opposite-spin energy of
+    the supercell is E_OS = -int_0^inf S(tau) dtau, and E_SOS-MP2 = 1.3 E_OS (Eq. 11)."""
+    nk = chi.shape[0]
+    km = k_minus_table(kmesh)
+    tot = 0.0 + 0.0j
+    for Q in range(nk):
+        Vc = V[Q].conj()
+        tot += np.trace(Vc @ chi[Q] @ Vc @ chi[km[0, Q]].T)
+    return float((nk * nk * tot).real)
 
 
 # ----------------------------------------------------------------------------

@@ -38,6 +38,7 @@ TAG_GAMMA = 3
 TAG_SIZES = 4
 TAG_REAL = 5
 TAG_SINGLEK = 6
+TAG_EPS = 7
 
 SEED_BASE = 20260000
 
@@ -160,6 +161,17 @@ def mo_coefficients(cell: Cell, seed: int) -> np.ndarray:
     rng = _rng(seed, TAG_MO)
     g = _cgauss(rng, (nk, nao, nao))
     return np.stack([_qr_pos(g[k]) for k in range(nk)])
+
+
+def orbital_energies(cell: Cell, seed: int, n_occ: int) -> np.ndarray:
+    """Seeded synthetic orbital energies per k (Ha), ascending, the first n_occ
+    occupied in [-1.0, -0.2] and the rest virtual in [0.2, 2.0] (a gap around
+    the chemical potential 0), shape (Nk, N_AO).  Stand-ins for k-HF energies."""
+    nk, nao = cell.nkpts, cell.nao
+    rng = _rng(seed, TAG_EPS)
+    occ = np.sort(rng.uniform(-1.0, -0.2, size=(nk, n_occ)), axis=1)
+    vir = np.sort(rng.uniform(0.2, 2.0, size=(nk, nao - n_occ)), axis=1)
+    return np.concatenate([occ, vir], axis=1)
 
 
 def make_fragment(cell: Cell, seed: int, index: int, norb: int,

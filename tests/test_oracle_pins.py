@@ -375,6 +375,86 @@ def test_ao_quartet_symmetries_and_momentum(tiny5):
         O.ao_eri(r["X"], r["V"], [(k1, k2, k3, kp[k4, 1])], cell.kmesh)
 
 
+@pytest.fixture(scope="module")
+def sos_case(tiny5):
+    """tiny5 fit with synthetic k-HF stand-ins: seeded orbitals and energies, 2 occupied per k."""
+    cell, phi, ips, nf = tiny5
+    r = O.run_isdf(cell, 12, 7, solve_tol=1e-10, ips=ips[:12], phi=phi)
+    C = W.mo_coefficients(cell, 5)
+    eps = W.orbital_energies(cell, 5, 2)
+    return cell, r, C, eps, 2
+
+
+def _sos_mo_sum(cell, r, C, eps, nocc, tau=None):
+    """sum over occupied i, j and virtual a, b (all k, momentum-conserving) of
+    |(ia|jb)|^2 exp(-tau Delta), or |(ia|jb)|^2 / Delta when tau is None, with the
+    MO integrals from Eq. 9 applied to Y = X C."""
+    Y = np.einsum("kim,kmn->kin", r["X"], C)
+    kp, km = O.k_plus_table(cell.kmesh), O.k_minus_table(cell.kmesh)
+    nk, tot = cell.nkpts, 0.0
+    for ki in range(nk):
+        for ka in range(nk):
+            for kj in range(nk):
+                kb = kp[kj, km[ki, ka]]
+                e = O.ao_eri(Y, r["V"], [(ki, ka, kj, kb)], cell.kmesh)[0][:nocc, nocc:, :nocc, nocc:]
+                d = (eps[ka, nocc:][None, :, None, None] - eps[ki, :nocc][:, None, None, None]
+                     + eps[kb, nocc:][None, None, None, :] - eps[kj, :nocc][None, None, :, None])
+                tot += (np.abs(e) ** 2 * (1.0 / d if tau is None else np.exp(-tau * d))).sum()
+    return tot
+
+
+def _sos_S(cell, r, C, eps, nocc, tau):
+    Go, Gv = O.green_ip(r["X"], C, eps, nocc, tau)
+    return O.sos_trace(O.polarizability(Go, Gv, cell.kmesh), r["V"], cell.kmesh)
+
+
+def test_sos_trace_equals_mo_sum(sos_case):
+    """Eqs. 12-15: tr over q of P^q P^q with P = chi V equals the sum over
+    occupied/virtual pairs of |(ia|jb)|^2 exp(-tau Delta) built from Eq. 9."""
+    cell, r, C, eps, nocc = sos_case
+    for tau in (0.0, 0.7, 2.5):
+        ref = _sos_mo_sum(cell, r, C, eps, nocc, tau)
+        assert abs(_sos_S(cell, r, C, eps, nocc, tau) - ref) < 1e-10 * ref
+
+
+def test_sos_laplace_integral_is_mp2_denominator(sos_case):
+    """int_0^inf S(tau) dtau = sum |(ia|jb)|^2 / (eps_a + eps_b - eps_i - eps_j):
+    the Laplace form of the opposite-spin MP2 energy (E_OS = -this)."""
+    from scipy.integrate import quad
+    cell, r, C, eps, nocc = sos_case
+    val, err = quad(lambda t: _sos_S(cell, r, C, eps, nocc, t), 0.0, np.inf, epsabs=0.0, epsrel=1e-11, limit=200)
+    ref = _sos_mo_sum(cell, r, C, eps, nocc, None)
+    assert abs(val - ref) < 1e-8 * ref
+
+
+def test_polarizability_hermitian_psd(sos_case):
+    cell, r, C, eps, nocc = sos_case
+    Go, Gv = O.green_ip(r["X"], C, eps, nocc, 0.9)
+    chi = O.polarizability(Go, Gv, cell.kmesh)
+    for Q in range(cell.nkpts):
+        h = chi[Q]
+        assert np.abs(h - h.conj().T).max() < 1e-12 * np.abs(h).max()
+        assert np.linalg.eigvalsh(h).min() > -1e-10 * np.abs(h).max()
+
+
+def test_mutation_polarizability_index_caught(sos_case, monkeypatch):
+    """k + Q in place of k - Q in the convolution breaks the MO-sum identity."""
+    cell, r, C, eps, nocc = sos_case
+    kp = O.k_plus_table(cell.kmesh)
+
+    def mutant(Go, Gv, kmesh):
+        out = np.zeros_like(Go)
+        for Q in range(Go.shape[0]):
+            for k in range(Go.shape[0]):
+                out[Q] += Go[k].T * Gv[kp[k, Q]]
+        return out
+
+    ref = _sos_mo_sum(cell, r, C, eps, nocc, 0.7)
+    Go, Gv = O.green_ip(r["X"], C, eps, nocc, 0.7)
+    bad = O.sos_trace(mutant(Go, Gv, cell.kmesh), r["V"], cell.kmesh)
+    assert abs(bad - ref) > 1e-6 * ref
+
+
 def test_eri_symmetries(c1run):
     wl, r = c1run
     f = W.make_fragment(wl.cell, wl.seed, 3, 5)
