@@ -188,6 +188,25 @@ int isdf_exchange(isdf_handle* h, const void* P, void* K_out);
  * Needs the Coulomb metric (either route). */
 int isdf_ao_eri(isdf_handle* h, int n_quartet, const int32_t* quartets, void* out);
 
+/* k-SOS-MP2 building blocks at one imaginary time tau >= 0 (Eqs. 11-15), FP64.
+ * With orbital values at the points Y^k = X^k C^k and energies measured from a
+ * chemical potential inside the gap:
+ *   Go^k(tau) = Y_occ e^{+tau eps_i} Y_occ^H,   Gv^k(tau) = Y_vir e^{-tau eps_a} Y_vir^H,
+ *   chi^Q_{IK}(tau) = sum_k Go^k_{KI}(tau) Gv^{k-Q}_{IK}(tau)      (P^Q = chi^Q V^Q),
+ *   S(tau) = Nk^2 sum_Q tr[conj(V^Q) chi^Q conj(V^Q) (chi^{-Q})^T]
+ *          = sum_{ia,jb} |(ia|jb)|^2 exp(-tau (eps_a - eps_i + eps_b - eps_j))
+ * over the supercell, so that E_OS = -int_0^inf S(tau) dtau and
+ * E_SOS-MP2 = 1.3 E_OS (Eq. 11).  The quadrature over tau is the caller's.
+ * (The printed signs of Eq. 15 grow with tau; these are the decaying ones that
+ * reproduce the Laplace form of the opposite-spin MP2 sum.)
+ *   C        device complex128 [Nk][N_AO][n_mo] orbital coefficients per k
+ *   eps      host double [Nk][n_mo] orbital energies; orbitals 0..n_occ-1 occupied
+ *   chi_out  device complex128 [Nk][N_P][N_P], or NULL
+ *   s_out    host double (S(tau)), or NULL
+ * Needs the Coulomb metric (either route). */
+int isdf_sos_polarizability(isdf_handle* h, const void* C, int n_mo, int n_occ, const double* eps, double tau,
+                            void* chi_out, double* s_out);
+
 /* Time-reversal pairing (default on).  The AO basis is real and the k-mesh
  * Gamma-centred, so Pi^{-q} = conj(Pi^q) and eta^{-q} = conj(eta^q) (Eqs. 4-5),
  * hence zeta^{-q} = conj(zeta^q) and V^{-q} = conj(V^q); and for any orbitals

@@ -25,7 +25,7 @@ STATUS = {0: "ISDF_OK", -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_OOM", -3: "ISDF_ERR_CU
 # Every entry point declared in include/isdf.h.
 EXPORTS = ["isdf_create", "isdf_build_points", "isdf_set_points", "isdf_fit_zeta",
            "isdf_coulomb_metric", "isdf_coulomb_metric_eta", "isdf_fragment_eri", "isdf_exchange",
-           "isdf_ao_eri",
+           "isdf_ao_eri", "isdf_sos_polarizability",
            "isdf_set_time_reversal", "isdf_set_workspace_limit", "isdf_get", "isdf_sizes",
            "isdf_launch_count", "isdf_timing_enable", "isdf_timing_get", "isdf_eri_traces_noalloc",
            "isdf_last_error", "isdf_destroy"]
@@ -67,6 +67,7 @@ def load(path: Optional[str] = None) -> ct.CDLL:
     lib.isdf_fragment_eri.argtypes = [vp, ct.c_int, i32p, ct.POINTER(vp), ct.POINTER(vp), ct.POINTER(vp), dp, dp]
     lib.isdf_exchange.argtypes = [vp, vp, vp]
     lib.isdf_ao_eri.argtypes = [vp, ct.c_int, i32p, vp]
+    lib.isdf_sos_polarizability.argtypes = [vp, vp, ct.c_int, ct.c_int, dp, ct.c_double, vp, dp]
     lib.isdf_set_time_reversal.argtypes = [vp, ct.c_int]
     lib.isdf_set_workspace_limit.argtypes = [vp, ct.c_uint64]
     lib.isdf_get.argtypes = [vp, ct.c_int, vp]
@@ -225,6 +226,15 @@ class Isdf:
         self._check(self.lib.isdf_ao_eri(self.h, int(q.shape[0]), q.ctypes.data_as(ct.POINTER(ct.c_int32)),
                                          _ptr(out)))
         return out
+
+    def sos_polarizability(self, C, eps, n_occ: int, tau: float, chi_out=None) -> float:
+        """k-SOS-MP2 polarisability chi^Q(tau) (into chi_out, if given) and S(tau) (Eqs. 11-15)."""
+        e = np.ascontiguousarray(np.asarray(eps, np.float64))
+        s = ct.c_double()
+        self._check(self.lib.isdf_sos_polarizability(
+            self.h, _ptr(C), int(C.shape[-1]), int(n_occ), e.ctypes.data_as(ct.POINTER(ct.c_double)),
+            float(tau), _ptr(chi_out), ct.byref(s)))
+        return s.value
 
     def get(self, what: int, out):
         self._check(self.lib.isdf_get(self.h, int(what), _ptr(out)))

@@ -190,6 +190,13 @@ cudaError_t scale_blocks(cudaStream_t st, const double2* L, int64_t per, int nb,
 cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, float2* out);
 // out[I][mu n_ao + nu] = conj(x1[I][mu]) x2[I][nu] for I < np (x1, x2: [np][n_ao]).
 cudaError_t ao_pairs(cudaStream_t st, const double2* x1, const double2* x2, int np, int nao, double2* out);
+// k-SOS-MP2 pieces: weighted orbital columns, the k-convolution of the Green's
+// functions, and the per-Q partial traces of the opposite-spin energy.
+cudaError_t scale_cols(cudaStream_t st, const double2* y, int nk, int np, int nmo, int c0, int nc, const double* eps,
+                       double sgn_tau, double2* out);
+cudaError_t chi_kconv(cudaStream_t st, const double2* go, const double2* gv, const int kmesh[3], int np, double2* chi);
+cudaError_t sos_trace_parts(cudaStream_t st, const double2* t, const double2* chi, const int kmesh[3], int np,
+                            double* part);
 // x[pairs[i].x] = conj(x[pairs[i].y]) for blocks of `per` elements.
 cudaError_t mirror_conj(cudaStream_t st, double2* x, int64_t per, const int2* pairs, int npairs);
 // out[b][I][J] = a[b][J][I] * c[b][I][J] for nb blocks of n x n.

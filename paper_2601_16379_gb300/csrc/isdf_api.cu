@@ -981,6 +981,60 @@ int isdf_ao_eri(isdf_handle* h, int n_quartet, const int32_t* quartets, void* ou
   return ISDF_OK;
 }
 
+int isdf_sos_polarizability(isdf_handle* h, const void* C, int n_mo, int n_occ, const double* eps, double tau,
+                            void* chi_out, double* s_out) {
+  if (!h) return ISDF_ERR_ARG;
+  LaunchScope ls(h);
+  if (int e = check_device(h)) return e;
+  if (!h->has_coulomb) return fail(h, ISDF_ERR_STATE, "isdf_sos_polarizability before the Coulomb metric");
+  if (!C || !eps || n_mo < 1 || n_occ < 1 || n_occ >= n_mo || !(tau >= 0.0) || !std::isfinite(tau))
+    return fail(h, ISDF_ERR_ARG, "isdf_sos_polarizability: need C, eps, 0 < n_occ < n_mo and finite tau >= 0");
+  const int nk = h->nk, np = h->np, nao = h->nao, nvir = n_mo - n_occ;
+  const int64_t pp = (int64_t)np * np;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  double2* X = (double2*)h->buf("X");
+  double2* Lq = (double2*)h->buf("Lq");
+  ENSURE(epsd, double, "sos_eps", (size_t)nk * n_mo);
+  ENSURE(Y, double2, "sos_y", (size_t)nk * np * n_mo);
+  ENSURE(Yo, double2, "sos_yo", (size_t)nk * np * n_occ);
+  ENSURE(Yv, double2, "sos_yv", (size_t)nk * np * nvir);
+  ENSURE(Go, double2, "sos_go", (size_t)nk * pp);
+  ENSURE(Gv, double2, "sos_gv", (size_t)nk * pp);
+  ENSURE(chi_w, double2, "sos_chi", (size_t)nk * pp);
+  ENSURE(Vq, double2, "sos_v", (size_t)nk * pp);
+  ENSURE(T1, double2, "sos_t1", (size_t)nk * pp);
+  ENSURE(part, double, "sos_part", nk);
+  double2* chi = chi_out ? (double2*)chi_out : chi_w;
+  CK(cudaMemcpyAsync(epsd, eps, sizeof(double) * (size_t)nk * n_mo, cudaMemcpyHostToDevice, h->st));
+  // Y^k = X^k C^k (orbital values at the points, Eq. 14)
+  CK(zgemm(h->st, 'N', 'N', np, n_mo, nao, one, X, nao, (int64_t)np * nao, (const double2*)C, n_mo,
+           (int64_t)nao * n_mo, zero, Y, n_mo, (int64_t)np * n_mo, nk));
+  // Go^k = Y_occ e^{+tau eps_i} Y_occ^H,  Gv^k = Y_vir e^{-tau eps_a} Y_vir^H (Eq. 15)
+  CK(scale_cols(h->st, Y, nk, np, n_mo, 0, n_occ, epsd, +tau, Yo));
+  CK(scale_cols(h->st, Y, nk, np, n_mo, n_occ, nvir, epsd, -tau, Yv));
+  CK(zgemm(h->st, 'N', 'C', np, np, n_occ, one, Yo, n_occ, (int64_t)np * n_occ, Y, n_mo, (int64_t)np * n_mo, zero,
+           Go, np, pp, nk));
+  CK(zgemm(h->st, 'N', 'C', np, np, nvir, one, Yv, nvir, (int64_t)np * nvir, Y + n_occ, n_mo, (int64_t)np * n_mo,
+           zero, Gv, np, pp, nk));
+  // chi^Q_{IK} = sum_k Go^k_{KI} Gv^{k-Q}_{IK} (Eq. 13)
+  CK(chi_kconv(h->st, Go, Gv, h->cell.kmesh, np, chi));
+  if (s_out) {
+    // S = Nk^2 sum_Q tr[conj(V^Q) chi^Q conj(V^Q) (chi^{-Q})^T], V^Q = L^Q L^Q^H (Eq. 12)
+    CK(zgemm(h->st, 'N', 'C', np, np, np, one, Lq, np, pp, Lq, np, pp, zero, Vq, np, pp, nk));
+    CK(zgemm(h->st, 'R', 'N', np, np, np, one, Vq, np, pp, chi, np, pp, zero, T1, np, pp, nk));
+    CK(zgemm(h->st, 'N', 'R', np, np, np, one, T1, np, pp, Vq, np, pp, zero, Go, np, pp, nk));  // Go reused
+    CK(sos_trace_parts(h->st, Go, chi, h->cell.kmesh, np, part));
+    std::vector<double> hp(nk);
+    CK(cudaMemcpyAsync(hp.data(), part, sizeof(double) * nk, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    double S = 0.0;
+    for (int q = 0; q < nk; ++q) S += hp[q];
+    *s_out = (double)nk * (double)nk * S;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return ISDF_OK;
+}
+
 int isdf_exchange(isdf_handle* h, const void* P, void* K_out) {
   if (!h || !P || !K_out) return fail(h, ISDF_ERR_ARG, "isdf_exchange: NULL argument");
   LaunchScope ls(h);

@@ -171,6 +171,64 @@ __global__ void ao_pair_kernel(const double2* __restrict__ x1, const double2* __
   }
 }
 
+// out[k][I][j] = y[k][I][c0 + j] exp(sgn tau eps[k][c0 + j]) for j < nc (columns of the
+// orbital values at the points weighted by the imaginary-time factors).
+__global__ void scale_cols_kernel(const double2* __restrict__ y, int nk, int np, int nmo, int c0, int nc,
+                                  const double* __restrict__ eps, double sgn_tau, double2* __restrict__ out) {
+  const int64_t total = (int64_t)nk * np * nc;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % nc);
+    const int64_t kI = e / nc;
+    const int k = (int)(kI / np);
+    const double w = exp(sgn_tau * eps[(int64_t)k * nmo + c0 + j]);
+    const double2 v = y[kI * nmo + c0 + j];
+    out[e] = make_double2(v.x * w, v.y * w);
+  }
+}
+
+// chi[Q][I][K] = sum_k go[k][K][I] gv[k - Q][I][K]  (direct k-convolution on the mesh)
+__global__ void chi_kconv_kernel(const double2* __restrict__ go, const double2* __restrict__ gv, int n0, int n1,
+                                 int n2, int np, double2* __restrict__ chi) {
+  const int nk = n0 * n1 * n2;
+  const int64_t pp = (int64_t)np * np, total = (int64_t)nk * pp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int Q = (int)(e / pp);
+    const int I = (int)((e % pp) / np), K = (int)(e % np);
+    const int q0 = Q / (n1 * n2), q1 = (Q / n2) % n1, q2 = Q % n2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < nk; ++k) {
+      const int k0 = k / (n1 * n2), k1 = (k / n2) % n1, k2 = k % n2;
+      const int m = (((k0 - q0 + n0) % n0) * n1 + (k1 - q1 + n1) % n1) * n2 + (k2 - q2 + n2) % n2;
+      const double2 a = go[(int64_t)k * pp + (int64_t)K * np + I], b = gv[(int64_t)m * pp + (int64_t)I * np + K];
+      acc.x += a.x * b.x - a.y * b.y;
+      acc.y += a.x * b.y + a.y * b.x;
+    }
+    chi[e] = acc;
+  }
+}
+
+// part[Q] = Re sum_IJ t[Q][I][J] chi[-Q][I][J]  (one block per Q, fixed summation order)
+__global__ void __launch_bounds__(256) sos_trace_kernel(const double2* __restrict__ t, const double2* __restrict__ chi,
+                                                        int n0, int n1, int n2, int np, double* __restrict__ part) {
+  const int Q = blockIdx.x;
+  const int q0 = Q / (n1 * n2), q1 = (Q / n2) % n1, q2 = Q % n2;
+  const int mQ = (((n0 - q0) % n0) * n1 + (n1 - q1) % n1) * n2 + (n2 - q2) % n2;
+  const int64_t pp = (int64_t)np * np;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < pp; e += blockDim.x) {
+    const double2 a = t[(int64_t)Q * pp + e], b = chi[(int64_t)mQ * pp + e];
+    acc += a.x * b.x - a.y * b.y;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[Q] = sh[0];
+}
+
 __global__ void z2c_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = make_float2((float)in[e].x, (float)in[e].y);
@@ -250,6 +308,27 @@ cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int n
 
 cudaError_t ao_pairs(cudaStream_t st, const double2* x1, const double2* x2, int np, int nao, double2* out) {
   ao_pair_kernel<<<nblocks((int64_t)np * nao * nao), 256, 0, st>>>(x1, x2, np, nao, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t scale_cols(cudaStream_t st, const double2* y, int nk, int np, int nmo, int c0, int nc, const double* eps,
+                       double sgn_tau, double2* out) {
+  if ((int64_t)nk * np * nc == 0) return cudaSuccess;
+  scale_cols_kernel<<<nblocks((int64_t)nk * np * nc), 256, 0, st>>>(y, nk, np, nmo, c0, nc, eps, sgn_tau, out);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t chi_kconv(cudaStream_t st, const double2* go, const double2* gv, const int kmesh[3], int np, double2* chi) {
+  const int nk = kmesh[0] * kmesh[1] * kmesh[2];
+  chi_kconv_kernel<<<nblocks((int64_t)nk * np * np), 256, 0, st>>>(go, gv, kmesh[0], kmesh[1], kmesh[2], np, chi);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t sos_trace_parts(cudaStream_t st, const double2* t, const double2* chi, const int kmesh[3], int np,
+                            double* part) {
+  const int nk = kmesh[0] * kmesh[1] * kmesh[2];
+  sos_trace_kernel<<<nk, 256, 0, st>>>(t, chi, kmesh[0], kmesh[1], kmesh[2], np, part);
   count_launch();
   return cudaGetLastError();
 }

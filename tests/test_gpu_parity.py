@@ -335,6 +335,41 @@ def test_ao_quartet_eri_matches_oracle(cuda, lib_built, c1, aniso, case):
     g.close()
 
 
+@pytest.mark.parametrize("case", ["c1", "aniso"])
+def test_sos_polarizability_matches_oracle(cuda, lib_built, c1, aniso, case):
+    """k-SOS-MP2 polarisability chi^Q(tau) for every Q and the opposite-spin trace
+    S(tau) (Eqs. 11-15) against the oracle's direct k-sums, with seeded stand-ins
+    for the k-HF orbitals and energies."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    if case == "c1":
+        wl, o = c1
+        cell = wl.cell
+    else:
+        cell, o = aniso
+    tol = 1e-7
+    _, _, V = o.fit(tol)
+    C = W.mo_coefficients(cell, 17)
+    n_occ = 3
+    eps = W.orbital_energies(cell, 17, n_occ)
+    g = B.Isdf(cell, B.ISDF_FP64)
+    g.set_points(o.ips)
+    g.fit_zeta(tol)
+    g.coulomb_metric()
+    nk, npp = cell.nkpts, len(o.ips)
+    Cd = _dev(torch, C)
+    for tau in (0.0, 0.6):
+        Go, Gv = O.green_ip(o.X, C, eps, n_occ, tau)
+        chi_ref = O.polarizability(Go, Gv, cell.kmesh)
+        s_ref = O.sos_trace(chi_ref, V, cell.kmesh)
+        chi = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
+        s = g.sos_polarizability(Cd, eps, n_occ, tau, chi)
+        got = chi.cpu().numpy()
+        assert np.abs(got - chi_ref).max() <= 1e-12 * np.abs(chi_ref).max()
+        assert abs(s - s_ref) <= 1e-8 * abs(s_ref)
+    g.close()
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7)])
 def test_eri_c2(cuda, lib_built, c2, prec, tol):
     from paper_2601_16379_gb300 import binding as B
