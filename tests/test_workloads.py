@@ -43,3 +43,13 @@ def test_real_and_singlek_fragments():
     for p in range(6):
         nz = np.nonzero(np.abs(g.C[:, :, p]).sum(axis=1))[0]
         assert list(nz) == [kp[p]]
+
+
+def test_orbital_energies_seeded_with_a_gap():
+    wl = W.workload("c1", with_fragments=False)
+    e1 = W.orbital_energies(wl.cell, 5, 3)
+    e2 = W.orbital_energies(wl.cell, 5, 3)
+    assert np.array_equal(e1, e2)
+    assert e1.shape == (wl.cell.nkpts, wl.cell.nao)
+    assert (e1[:, :3] <= -0.2).all() and (e1[:, 3:] >= 0.2).all()
+    assert (np.diff(e1[:, :3], axis=1) >= 0).all() and (np.diff(e1[:, 3:], axis=1) >= 0).all()
