@@ -141,11 +141,8 @@ cudaError_t pair_products_f(cudaStream_t st, const float2* t, int nk, int np, in
 
 // eri[p][q][r][s] = E[(p q)][(s r)] * scale, and the traces.
 cudaError_t eri_permute(cudaStream_t st, const double2* E, int nf, double scale, double2* eri);
-cudaError_t eri_permute_f(cudaStream_t st, const float2* E, int nf, float scale, float2* eri);
 cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale,
                        const double2* gamma, double* out2);
-cudaError_t eri_traces_f(cudaStream_t st, const float2* E, int nf, double scale,
-                         const double2* gamma, double* out2);
 
 // Message of the last failed handle-free call on this thread.
 const char* noalloc_last_error();
@@ -205,6 +202,5 @@ cudaError_t hadamard_t(cudaStream_t st, const double2* a, const double2* c, int 
 // Precision conversions.
 cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n);
 cudaError_t c2z(cudaStream_t st, const float2* in, double2* out, int64_t n);
-cudaError_t nonfinite_count(cudaStream_t st, const double* x, int64_t n, int32_t* flag);
 
 }  // namespace isdf

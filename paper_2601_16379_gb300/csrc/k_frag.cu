@@ -237,10 +237,6 @@ __global__ void c2z_kernel(const float2* __restrict__ in, double2* __restrict__ 
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = make_double2((double)in[e].x, (double)in[e].y);
 }
-__global__ void nonfinite_kernel(const double* __restrict__ x, int64_t n, int32_t* __restrict__ flag) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    if (!isfinite(x[e])) atomicOr(flag, 1);
-}
 
 inline int nblocks(int64_t total) {
   int64_t nb = (total + 255) / 256;
@@ -257,11 +253,6 @@ cudaError_t eri_permute(cudaStream_t st, const double2* E, int nf, double scale,
 }
 cudaError_t eri_permute_zc(cudaStream_t st, const double2* E, int nf, double scale, float2* eri) {
   eri_permute_kernel<double2, float2><<<nblocks((int64_t)nf * nf * nf * nf), 256, 0, st>>>(E, nf, scale, eri);
-  count_launch();
-  return cudaGetLastError();
-}
-cudaError_t eri_permute_f(cudaStream_t st, const float2* E, int nf, float scale, float2* eri) {
-  eri_permute_kernel<float2><<<nblocks((int64_t)nf * nf * nf * nf), 256, 0, st>>>(E, nf, scale, eri);
   count_launch();
   return cudaGetLastError();
 }
@@ -283,11 +274,6 @@ cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale, 
                        double* out) {
   double2* part = reinterpret_cast<double2*>(out + 4);
   return traces_impl<double2>(st, E, nf, scale, gamma, out, part);
-}
-cudaError_t eri_traces_f(cudaStream_t st, const float2* E, int nf, double scale, const double2* gamma,
-                         double* out) {
-  double2* part = reinterpret_cast<double2*>(out + 4);
-  return traces_impl<float2>(st, E, nf, scale, gamma, out, part);
 }
 
 cudaError_t eri_swapconj_sym(cudaStream_t st, double2* E, int nf) {
@@ -353,11 +339,6 @@ cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n) {
 }
 cudaError_t c2z(cudaStream_t st, const float2* in, double2* out, int64_t n) {
   c2z_kernel<<<nblocks(n), 256, 0, st>>>(in, out, n);
-  count_launch();
-  return cudaGetLastError();
-}
-cudaError_t nonfinite_count(cudaStream_t st, const double* x, int64_t n, int32_t* flag) {
-  nonfinite_kernel<<<nblocks(n), 256, 0, st>>>(x, n, flag);
   count_launch();
   return cudaGetLastError();
 }
