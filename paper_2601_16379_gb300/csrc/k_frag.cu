@@ -350,7 +350,7 @@ cudaError_t c2z(cudaStream_t st, const float2* in, double2* out, int64_t n) {
 // address, obtained once per device with cudaGetSymbolAddress.
 namespace {
 constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 20;  // 8 MiB: 4 + 4*n_f^2 doubles, n_f <= 511
-__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kMaxDevices] = {nullptr};
