@@ -437,6 +437,23 @@ def test_polarizability_hermitian_psd(sos_case):
         assert np.linalg.eigvalsh(h).min() > -1e-10 * np.abs(h).max()
 
 
+def test_polarizability_by_the_convolution_theorem(sos_case):
+    """The k-convolution of Eq. 13 by DFTs over the k-mesh (the form of Algorithm 1):
+    chi^Q = (1/Nk) sum_R a(R) b(R) e^{-i Q.R}, a(R) = sum_k Go^k^T e^{+i k.R},
+    b(R) = sum_k Gv^k e^{-i k.R}; equals the direct k-sum."""
+    cell, r, C, eps, nocc = sos_case
+    Go, Gv = O.green_ip(r["X"], C, eps, nocc, 0.4)
+    km = tuple(cell.kmesh)
+    nk, npp = Go.shape[0], Go.shape[1]
+    a = np.transpose(Go, (0, 2, 1)).reshape(km + (npp, npp))
+    b = Gv.reshape(km + (npp, npp))
+    aR = np.fft.ifftn(a, axes=(0, 1, 2)) * nk
+    bR = np.fft.fftn(b, axes=(0, 1, 2))
+    chi = np.fft.fftn(aR * bR, axes=(0, 1, 2)).reshape(nk, npp, npp) / nk
+    ref = O.polarizability(Go, Gv, cell.kmesh)
+    assert np.abs(chi - ref).max() < 1e-12 * np.abs(ref).max()
+
+
 def test_mutation_polarizability_index_caught(sos_case, monkeypatch):
     """k + Q in place of k - Q in the convolution breaks the MO-sum identity."""
     cell, r, C, eps, nocc = sos_case
