@@ -523,6 +523,62 @@ def test_traces_signs_and_cheap_J(c1run):
     assert abs(O.cheap_J(M, r["V"], f.gamma, wl.cell.nkpts) - ej) < 1e-9 * abs(ej)
 
 
+def _occupied(gamma):
+    """Orbital coefficients of the occupied space of gamma = 2 W W^H: columns of W."""
+    lam, U = np.linalg.eigh(gamma)
+    occ = lam > 1.0
+    assert np.allclose(lam[occ], 2.0) and np.allclose(lam[~occ], 0.0, atol=1e-12)
+    return U[:, occ]
+
+
+def _traces_from_orbitals(cell, frag):
+    """E_J = 2 sum_ij (ii|jj) and E_K = -sum_ij (ij|ji) over the doubly occupied
+    orbitals psi_i = sum_q conj(W_qi) phi_q of gamma = 2 W W^H (density
+    n = sum gamma_pq phi_p^* phi_q = 2 sum_i |psi_i|^2), from the grid-exact ERIs of
+    the psi themselves: no gamma contraction of fragment ERIs is involved."""
+    Wo = _occupied(frag.gamma)
+    Cpsi = np.einsum("kmq,qi->kmi", frag.C, Wo.conj())
+    g = O.fftdf_fragment_eri(cell, Cpsi)
+    no = Wo.shape[1]
+    ej = 2.0 * sum(g[i, i, j, j] for i in range(no) for j in range(no))
+    ek = -sum(g[i, j, j, i] for i in range(no) for j in range(no))
+    return float(ej.real), float(ek.real)
+
+
+def test_traces_equal_occupied_orbital_sums(tiny):
+    """E_J and E_K of the fragment-ERI contraction equal the Coulomb and exchange
+    sums over the occupied orbitals of gamma, at the pair-space rank where the
+    ISDF ERIs are grid-exact."""
+    cell, phi, ips, nf = tiny
+    frag = W.make_fragment(cell, 11, 0, 4)
+    r = O.run_isdf(cell, nf, 7, solve_tol=1e-14, ips=ips, phi=phi)
+    eri = O.fragment_eri(r["X"], r["V"], frag.C, cell.kmesh)
+    ej, ek = O.traces(eri, frag.gamma)
+    rj, rk = _traces_from_orbitals(cell, frag)
+    assert ek < 0 < ej
+    assert abs(ej - rj) < 1e-9 * abs(rj)
+    assert abs(ek - rk) < 1e-9 * abs(rk)
+
+
+def test_mutation_exchange_index_caught(tiny, monkeypatch):
+    """A slip in the exchange contraction (gamma_pr gamma_qs for gamma_ps gamma_rq)
+    is caught by the occupied-orbital pin."""
+    cell, phi, ips, nf = tiny
+    frag = W.make_fragment(cell, 11, 0, 4)
+    r = O.run_isdf(cell, nf, 7, solve_tol=1e-14, ips=ips, phi=phi)
+    eri = O.fragment_eri(r["X"], r["V"], frag.C, cell.kmesh)
+
+    def bad_traces(e, gamma):
+        ej = 0.5 * np.einsum("pq,rs,pqrs->", gamma, gamma, e)
+        ek = -0.25 * np.einsum("pr,qs,pqrs->", gamma, gamma, e)
+        return float(ej.real), float(ek.real)
+
+    monkeypatch.setattr(O.isdf_oracle, "traces", bad_traces)
+    _, ek = O.isdf_oracle.traces(eri, frag.gamma)
+    _, rk = _traces_from_orbitals(cell, frag)
+    assert abs(ek - rk) > 1e-3 * abs(rk)
+
+
 def test_nk1_is_gamma_point_isdf():
     """At Nk = 1 the fit is textbook Gamma-point ISDF of real pair products."""
     cell = tiny_cell(kmesh=1, mesh=10)
