@@ -11,11 +11,18 @@ The default workload is c5 (Nk = 10^3, 24^3 grid, N_P = 300, 64 fragments
 with n_f ~ U[40, 200]), the configuration the headline metric is quoted on;
 c1-c4 are smaller cases (parity tests, quicker timings).
 
+A c5 build takes tens of seconds, so the run keeps to a wall-clock budget
+(--budget-s, counted from process start): at least three warm-up steps, then
+timed steps while the remaining time still covers one more step, the
+end-to-end step and the checks after it.  The line reports the warm-up and
+timed step counts actually executed next to the requested ones.
+
 Prints one JSON line (rank 0).  `value` is seconds per fragment-ERI build
 (lower is better), timed with CUDA events on the library's stream between
-barriers, max over ranks.  Under torchrun each rank builds its own replica of
-the workload (weak scaling; the path shards by fragment without any
-collective, so replicas are the per-GPU unit).  `--impl reference` times the
+barriers, max over ranks.  Under torchrun the fragments are partitioned over
+the ranks (longest first by n_f^4; every rank builds X and V^q itself) and
+the traces gathered by one sum-reduction per step, so the ranks share one
+workload (strong scaling).  `--impl reference` times the
 FP64 oracle (direct k-sums) on the host cores on a bounded sample of the same
 workload and extrapolates by exact operation counts.
 """
@@ -34,6 +41,7 @@ from pathlib import Path
 
 import numpy as np
 
+T_PROCESS_START = time.perf_counter()
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
@@ -102,19 +110,21 @@ class ClockSampler:
 
 # ---------------------------------------------------------- profile lookup
 def profile_traffic(kernel_file: str, workload: str):
-    """dram bytes per launch from the committed ncu summary, or None if the
-    kernel source changed since the capture."""
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
+    or None.  A summary counts only if it records the same workload string
+    (overrides included) and the hash of the kernel source it was taken on."""
     src = ROOT / "paper_2601_16379_gb300" / "csrc" / kernel_file
-    prof = ROOT / "profiles" / f"herk_{workload}.md"
-    if not (src.exists() and prof.exists()):
+    if not src.exists():
         return None
-    text = prof.read_text()
     h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
-    m = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not (m and t) or m.group(1) != h:
-        return None
-    return float(t.group(1))
+    for prof in sorted((ROOT / "profiles").glob("*.md")):
+        text = prof.read_text()
+        m = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
+        w = re.search(r"^workload:\s*(.+)$", text, re.M)
+        t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        if m and w and t and m.group(1) == h and w.group(1).strip() == workload.strip():
+            return float(t.group(1))
+    return None
 
 
 def reduce_max_over_ranks(values, dist, device):
@@ -128,11 +138,33 @@ def reduce_max_over_ranks(values, dist, device):
 
 
 # ------------------------------------------------------------- GPU arm
+MIN_WARMUP = 3          # warm-up steps required before a timed step counts
+
+
+class Budget:
+    """Wall-clock plan of one bench run.  The whole command must end well inside
+    the caller's time limit, so warm-ups, timed steps, the end-to-end step and the
+    checks after it are each admitted only while the remaining time covers them
+    plus what must still follow."""
+
+    def __init__(self, total_s: float):
+        self.t0 = T_PROCESS_START
+        self.total = total_s
+
+    def elapsed(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def left(self) -> float:
+        return self.total - self.elapsed()
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2601_16379_gb300 import binding as B
+    from paper_2601_16379_gb300 import partition as P
     from paper_2601_16379_gb300 import workloads as W
 
+    budget = Budget(args.budget_s)
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -140,7 +172,10 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     prec = B.ISDF_MIXED if args.precision == "mixed" else B.ISDF_FP64
     wl = W.workload(args.workload, kmesh=args.kmesh, mesh=args.mesh, frag_sizes=_frag_sizes(args))
-    frags = wl.fragments
+    # fragment partition: every rank builds X and V^q, contracts its share of the
+    # fragments, and the traces are gathered (one sum-reduction per step)
+    mine = P.fragment_partition([f.norb for f in wl.fragments], world)[rank]
+    frags = [wl.fragments[i] for i in mine]
     g = B.Isdf(wl.cell, prec)
     dt_out = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
     Cs = [torch.from_numpy(f.C).cuda() for f in frags]
@@ -150,7 +185,9 @@ def run_gpu(args, rank, world, local_rank):
     # fragments are done one after the other on the stream)
     esz = torch.empty((), dtype=dt_out).element_size()
     out_bytes = sum(f.norb ** 4 for f in frags) * esz
-    if out_bytes <= OUT_SEPARATE_MAX:
+    if not frags:
+        outs, out_mode = [], "no fragments on this rank"
+    elif out_bytes <= OUT_SEPARATE_MAX:
         outs = [torch.empty((f.norb,) * 4, dtype=dt_out, device="cuda") for f in frags]
         out_mode = "one tensor per fragment"
     else:
@@ -158,21 +195,37 @@ def run_gpu(args, rank, world, local_rank):
         outs = [shared[: f.norb ** 4].view((f.norb,) * 4) for f in frags]
         out_mode = f"one reused buffer (all {len(frags)} ERI tensors: {out_bytes / 2**30:.0f} GiB)"
 
-    def step(C_list, g_list):
-        g.build_points(wl.n_p, wl.seed)
-        g.fit_zeta(args.solve_tol)
-        g.coulomb_metric()
-        return g.fragment_eri(C_list, g_list, outs)
+    ranks_q = {}
 
-    for _ in range(args.warmup):
-        step(Cs, gs)
-    torch.cuda.synchronize()
+    def step(C_list, g_list, eri_list):
+        g.build_points(wl.n_p, wl.seed)
+        ranks_q["r"] = g.fit_zeta(args.solve_tol)
+        g.coulomb_metric()
+        ej, ek = g.fragment_eri(C_list, g_list, eri_list) if C_list else ([], [])
+        if world == 1:
+            return ej, ek
+        return P.gather_traces(len(wl.fragments), mine, ej, ek, dist)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # ---- device-timed region (inputs resident in HBM)
+    # ---- warm-up: at least MIN_WARMUP steps (fewer only if fewer were asked for),
+    # up to --warmup while the budget keeps room for one timed step and the rest
+    warm = []
+    want_w = args.warmup
+    for i in range(want_w):
+        if i >= min(want_w, MIN_WARMUP) and warm and budget.left() < warm[-1] * (2 + 1.5) + args.reserve_s:
+            break
+        t0 = time.perf_counter()
+        step(Cs, gs, outs)
+        torch.cuda.synchronize()
+        warm.append(time.perf_counter() - t0)
+    t_step = min(warm) if warm else 0.0
+
+    # ---- device-timed region (inputs resident in HBM): one CUDA event per step,
+    # steps admitted while the budget covers one more step, the end-to-end step
+    # and the checks after it (at least one timed step always runs)
     clocks = ClockSampler(local_rank)
     clocks.start()
     g.timing(True)
@@ -180,37 +233,52 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
-        ej, ek = step(Cs, gs)
-    e1.record(st)
+    evs = [torch.cuda.Event(enable_timing=True)]
+    evs[0].record(st)
+    done = 0
+    while done < args.steps:
+        if done >= 1 and budget.left() < t_step * (1 + 1.5) + args.reserve_s:
+            break
+        ej, ek = step(Cs, gs, outs)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(st)
+        evs.append(e)
+        done += 1
+        if t_step == 0.0:
+            torch.cuda.synchronize()
+            t_step = evs[0].elapsed_time(evs[-1]) / 1e3
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = (g.launch_count() - launches0) // args.steps
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(done)]
+    ms = evs[0].elapsed_time(evs[-1]) / done
+    launches = (g.launch_count() - launches0) // done
     herk_ms, herk_n, herk_flops = g.stage_time(5)
     stage = {name: g.stage_time(i) for i, name in enumerate(["points", "fit", "coulomb", "pair_tensor", "B=ML", "E=BB^H"])}
     g.timing(False)
     clk = clocks.stop()
 
-    # ---- end to end: inputs from pinned host memory, traces back to host
+    # ---- end to end through the C ABI with host buffers: C and gamma copied from
+    # page-locked host memory, the ERIs written by the library straight into a
+    # page-locked host buffer (one buffer of the largest size, reused like the
+    # device one), the traces returned to host
     Ch = [torch.from_numpy(f.C).pin_memory() for f in frags]
     gh = [torch.from_numpy(f.gamma).pin_memory() for f in frags]
+    host_shared = torch.empty(max([f.norb for f in frags] + [1]) ** 4, dtype=dt_out, pin_memory=True)
+    houts = [host_shared[: f.norb ** 4].view((f.norb,) * 4) for f in frags]
     h2d = sum(x.numel() * x.element_size() for x in Ch + gh)
-    d2h = 16 * len(frags)
+    d2h = sum(f.norb ** 4 for f in frags) * esz + 16 * len(frags)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for d, hsrc in zip(Cs, Ch):
-            d.copy_(hsrc, non_blocking=True)
-        for d, hsrc in zip(gs, gh):
-            d.copy_(hsrc, non_blocking=True)
-        ej2, ek2 = step(Cs, gs)   # traces are copied to host inside the call
+    for d, hsrc in zip(Cs, Ch):
+        d.copy_(hsrc, non_blocking=True)
+    for d, hsrc in zip(gs, gh):
+        d.copy_(hsrc, non_blocking=True)
+    ej2, ek2 = step(Cs, gs, houts)   # ERIs land in host memory; traces are copied to host inside the call
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    del host_shared, houts
 
     ms, e2e_ms = reduce_max_over_ranks([ms, e2e_ms], dist, "cuda")
 
@@ -225,46 +293,61 @@ def run_gpu(args, rank, world, local_rank):
         bound, peak, peak_name = "alu", 1.20, "FP64 FMA measured on this GB300 (1.20 TFLOP/s)"
     herk_avg_ms = herk_ms / max(herk_n, 1)
     achieved = (herk_flops / max(herk_n, 1)) / (herk_avg_ms * 1e-3) / 1e12 if herk_n else None
+    workload_name = f"{args.workload}: {wl.description}" + _overrides(args)
+    r = ranks_q.get("r")
     result = {
         "metric": METRIC,
         "value": ms / 1e3,
         "unit": "s",
         "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
+        "steps": done,
+        "warmup": len(warm),
+        "steps_requested": args.steps,
+        "warmup_requested": args.warmup,
+        "budget_s": args.budget_s,
         "ms_per_step": ms,
+        "step_ms": [round(x, 1) for x in step_ms],
         "higher_is_better": False,
-        "scaling": "weak",
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None,
         "dtype": "f64 fit + f32/fp16-slice fragment contraction" if prec == B.ISDF_MIXED else "f64",
         "data": "synthetic (seeded cell, Gaussian basis and fragment orbitals)",
-        "config": {"workload": f"{args.workload}: {wl.description}" + _overrides(args), "precision": args.precision,
+        "config": {"workload": workload_name, "precision": args.precision,
                    "solve_tol": args.solve_tol, "fragments": len(frags),
                    "sum_nf4": int(sum(f.norb ** 4 for f in frags)),
+                   "rank_pi_q": {"min": int(r.min()), "max": int(r.max())} if r is not None else None,
                    "l2": "inputs larger than L2 (Phi, eta, xi, M, B each > 129 MB)",
                    "eri_out": out_mode,
-                   "parallelism": f"replica x{world}"},
-        "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                   "parallelism": (f"fragment partition x{world} (X, V^q on every rank; traces gathered)"
+                                   if world > 1 else "1 GPU")},
+        "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "eri_out": "page-locked host buffer of the largest fragment, reused"},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "fragment E = sum_q B^q B^q^H (stage 5)", "bound": bound, "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "peak_source": peak_name,
                      "algorithmic_flops_per_launch": herk_flops / max(herk_n, 1),
                      "avg_launch_ms": herk_avg_ms, "launches": herk_n,
-                     "traffic": profile_traffic("k_tc.cu", args.workload)},
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage.items()},
+                     "traffic": profile_traffic("k_tc.cu", workload_name)},
+        "stages_ms_per_step": {k: v[0] / done for k, v in stage.items()},
         "clocks": clk,
         "traces_fragment0": {"E_J": float(ej[0]), "E_K": float(ek[0])},
     }
+    fit_s = sum(stage[k][0] for k in ("points", "fit", "coulomb")) / done / 1e3
     if rank == 0 and prec == B.ISDF_MIXED and not args.no_accuracy:
         # outside the timed region: free this handle's HBM, then compare against the FP64 path
-        del outs
-        g.close()
-        torch.cuda.empty_cache()
-        result["accuracy"] = accuracy_vs_fp64(wl, args.solve_tol)
+        est = accuracy_cost_s(wl, fit_s)
+        if budget.left() > est + CPU_BASELINE_S:
+            del outs
+            g.close()
+            torch.cuda.empty_cache()
+            result["accuracy"] = accuracy_vs_fp64(wl, args.solve_tol)
+        else:
+            result["accuracy"] = {"skipped": f"wall-clock budget ({budget.left():.0f} s left, ~{est:.0f} s needed)"}
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget, kmesh=args.kmesh,
                                               mesh=args.mesh, frag_sizes=_frag_sizes(args))
+    result["wall_s"] = round(budget.elapsed(), 1)
     if rank == 0:
         print(json.dumps(result))
     if dist is not None:
@@ -288,6 +371,7 @@ def _overrides(args):
 
 # ------------------------------------------------ mixed vs FP64 accuracy
 FP64_FLOP_BUDGET = 3e13   # FP64 E = B B^H work per sampled fragment (~25 s at 1.2 TFLOP/s)
+CPU_BASELINE_S = 40.0     # wall time kept for the oracle sample after the GPU work
 
 
 def _paired_q_count(kmesh):
@@ -300,6 +384,17 @@ def _paired_q_count(kmesh):
             if 2 * m0 <= n0 and (not self0 or 2 * m1 <= n1):
                 cnt += n2
     return cnt
+
+
+def accuracy_cost_s(wl, fit_s):
+    """Rough wall time of accuracy_vs_fp64: the points, fit and Coulomb metric in
+    both precisions (the FP64 Coulomb GEMM is slower) plus the FP64 contraction of
+    the sampled fragments at ~1 TFLOP/s."""
+    nsum = _paired_q_count(wl.cell.kmesh)
+    sizes = [f.norb for f in wl.fragments]
+    fl = [4.0 * (s * s) ** 2 * nsum * wl.n_p for s in sizes]
+    ok = [x for x in fl if x <= FP64_FLOP_BUDGET]
+    return 4.0 * fit_s + (max(ok) if ok else 0.0) / 1.0e12 + min(fl) / 1.0e12 + 30.0
 
 
 def accuracy_vs_fp64(wl, solve_tol):
@@ -435,6 +530,10 @@ def cpu_baseline(workload: str, budget_s: float = 20.0, kmesh=None, mesh=None, f
 def run_reference(args, rank):
     if rank != 0:
         return
+    from paper_2601_16379_gb300 import workloads as W
+    wl = W.workload(args.workload, kmesh=args.kmesh, mesh=args.mesh, frag_sizes=_frag_sizes(args),
+                    with_fragments=False)
+    workload_name = f"{args.workload}: {wl.description}" + _overrides(args)
     t0 = time.perf_counter()
     for _ in range(args.warmup):
         cpu_baseline(args.workload, kmesh=args.kmesh, mesh=args.mesh, frag_sizes=_frag_sizes(args))
@@ -447,7 +546,7 @@ def run_reference(args, rank):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "precision": "fp64 oracle (direct k-sums)"},
+           "config": {"workload": workload_name, "precision": "fp64 oracle (direct k-sums)"},
            "cpu_baseline": base,
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": time.perf_counter() - t0}
@@ -464,6 +563,11 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--solve-tol", type=float, default=SOLVE_TOL)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--budget-s", type=float, default=1200.0,
+                    help="wall-clock seconds for the whole run (from process start); warm-ups and timed steps "
+                         "beyond what fits are skipped and the executed counts reported")
+    ap.add_argument("--reserve-s", type=float, default=180.0,
+                    help="seconds kept after the timed steps for the accuracy check and the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed vs FP64 comparison")
     ap.add_argument("--kmesh", type=int, default=None, help="k-mesh side override (Nk scan)")

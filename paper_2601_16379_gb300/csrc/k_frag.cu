@@ -44,8 +44,11 @@ __global__ void __launch_bounds__(256) traces_rows_kernel(const T* __restrict__ 
   const int p = (int)(pq / nf), q = (int)(pq % nf);
   double2 aj = make_double2(0, 0), ak = make_double2(0, 0);
   for (int64_t sr = threadIdx.x; sr < n2; sr += blockDim.x) {
-    const int s = (int)(sr / nf), r = (int)(sr % nf);
-    const T ev = kChemist ? E[pq * n2 + (int64_t)r * nf + s] : E[pq * n2 + sr];  // = (pq|rs)
+    // consecutive threads take consecutive elements of the row in either layout:
+    // E[(pq)][(sr)] (s slow, r fast) or eri[p][q][r][s] (r slow, s fast)
+    const int s = kChemist ? (int)(sr % nf) : (int)(sr / nf);
+    const int r = kChemist ? (int)(sr / nf) : (int)(sr % nf);
+    const T ev = E[pq * n2 + sr];  // = (pq|rs)
     const double2 e2 = make_double2((double)ev.x, (double)ev.y);
     // J: gamma_rs * (pq|rs)
     const double2 grs = g[(int64_t)r * nf + s];
@@ -322,6 +325,13 @@ cudaError_t sos_trace_parts(cudaStream_t st, const double2* t, const double2* ch
 cudaError_t mirror_conj(cudaStream_t st, double2* x, int64_t per, const int2* pairs, int npairs) {
   if (npairs <= 0 || per <= 0) return cudaSuccess;
   mirror_kernel<double2, true><<<nblocks(per * npairs), 256, 0, st>>>(x, per, pairs, npairs);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mirror_copy(cudaStream_t st, int32_t* x, int64_t per, const int2* pairs, int npairs) {
+  if (npairs <= 0 || per <= 0) return cudaSuccess;
+  mirror_kernel<int32_t, false><<<nblocks(per * npairs), 256, 0, st>>>(x, per, pairs, npairs);
   count_launch();
   return cudaGetLastError();
 }
