@@ -147,36 +147,41 @@ cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale,
 // Message of the last failed handle-free call on this thread.
 const char* noalloc_last_error();
 
-// Tensor-core E = scale * B B^H (k_tc.cu); B complex64 n2 x K with row pitch ldb,
-// E complex128 n2 x n2 (full Hermitian).  Workspace sizes from the helpers below.
-size_t herk_tc_split_bytes(int64_t n2, int64_t K);
-void herk_tc_tiles(int64_t n2, std::vector<int2>& tiles);
-size_t herk_tc_ws_bytes(int64_t ntiles);
-cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int64_t ldb, double scale,
-                    void* split, const int2* tiles_d, int ntiles, void* ws, int* row_exp, int* err, double2* E);
-// The same in steps, for B addressed as (a, k = Q nJ + J) -> B[slot(Q) sQ + a sA + J]
-// with slot(Q) = qmap[Q] (or Q when qmap is NULL) and split into K chunks: row
-// exponents over all K, then each chunk (accumulate = 0 for the first), then the finish.
-cudaError_t herk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                             int64_t n2, int64_t K, int* row_exp);
-cudaError_t herk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                          int64_t n2, int64_t k0, int64_t Kc, const int* row_exp, void* split, const int2* tiles_d,
-                          int ntiles, void* ws, int accumulate, int* err);
-cudaError_t herk_tc_finish(cudaStream_t st, const void* ws, const int2* tiles_d, int ntiles, int64_t n2,
+// Tensor-core E = sum_q B^q B^q^H (k_tc.cu) in the real symmetric form of the
+// time-reversal basis.  B is addressed as (a, k = Q nJ + J) -> B[slot(Q) sQ + a sA + J]
+// with slot(Q) = qmap[Q] (or Q when qmap is NULL), J < nJ, over the nS positions
+// of the sum.  orb: the swap orbits of pair_orbits (device copy, n_f (n_f+1)/2 entries).
+// Row exponents over all positions, then each chunk of positions (accumulate = 0
+// for the first), then the finish to E (complex128 n_f^2 x n_f^2, full) times scale.
+void pair_orbits(int nf, std::vector<int2>& orb);
+size_t syrk_tc_split_bytes(int64_t n2, int64_t kcols);
+void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_of);
+size_t syrk_tc_ws_bytes(int64_t ntiles);
+cudaError_t syrk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                             int nS, const int2* orb, int nf, int* row_exp);
+cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                          const int2* orb, int nf, int j0, int nq, const int* row_exp, void* split,
+                          const int2* tiles_d, int ntiles, void* ws, int accumulate, int* err);
+cudaError_t syrk_tc_finish(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb, int nf,
                            const int* row_exp, double scale, double2* E);
 // B^q = M^q L^q (w_q^{1/2} folded into L) on the tensor cores with four exact
-// integer slices, written in place over M^q.  prepare: slices of L for all q
-// (once per L); chunk: the q-points j0..j0+nq-1 of the sum (slot qmap[j]).
-int mlgemm_tc_kp(int np);
-int mlgemm_tc_np_pad(int np);
-bool mlgemm_tc_supported(int np);
-size_t mlgemm_tc_lslice_bytes(int nk, int np);
-size_t mlgemm_tc_split_bytes(int64_t n2, int np, int nq);
-cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, void* lsl,
-                              int* col_exp);
-cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* qmap, int64_t n2, int np, int j0,
-                            int nq, const int* row_exp, void* split, const void* lsl, const int* col_exp, int nk,
-                            int* err);
+// integer slices, over the structural nonzeros of L^q only: the rp = max_q r_q
+// pivot columns perm_q[c] (c < rank_q) of M^q and the nj output columns; written
+// in place over M^q with row pitch nj.  prepare: slices of L for all q (once per
+// L); rowscale: exponents of the gathered M rows over the sum; chunk: the
+// positions j0..j0+nq-1 of the sum (q = qmap[j]).
+int mlgemm_tc_kp(int rp);
+int mlgemm_tc_nj_pad(int nj);
+bool mlgemm_tc_supported(int rp);
+size_t mlgemm_tc_lslice_bytes(int nk, int rp, int nj);
+size_t mlgemm_tc_split_bytes(int64_t n2, int rp, int nq);
+cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, const int* perm,
+                              const int* rank, int rp, int nj, void* lsl, int* col_exp);
+cudaError_t mlgemm_tc_rowscale(cudaStream_t st, const float2* M, int64_t sq, int np, const int* qmap, int nS,
+                               const int* perm, const int* rank, int rp, int64_t n2, int* row_exp);
+cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* qmap, int64_t n2, int np,
+                            const int* perm, const int* rank, int rp, int nj, int j0, int nq, const int* row_exp,
+                            void* split, const void* lsl, const int* col_exp, int nk, int* err);
 // eri[p][q][r][s] (complex64) = E[(p q)][(s r)] (complex128) * scale
 cudaError_t eri_permute_zc(cudaStream_t st, const double2* E, int nf, double scale, float2* eri);
 
@@ -194,8 +199,9 @@ cudaError_t scale_cols(cudaStream_t st, const double2* y, int nk, int np, int nm
 cudaError_t chi_kconv(cudaStream_t st, const double2* go, const double2* gv, const int kmesh[3], int np, double2* chi);
 cudaError_t sos_trace_parts(cudaStream_t st, const double2* t, const double2* chi, const int kmesh[3], int np,
                             double* part);
-// x[pairs[i].x] = conj(x[pairs[i].y]) for blocks of `per` elements.
+// x[pairs[i].x] = conj(x[pairs[i].y]) for blocks of `per` elements (mirror_copy: plain copy).
 cudaError_t mirror_conj(cudaStream_t st, double2* x, int64_t per, const int2* pairs, int npairs);
+cudaError_t mirror_copy(cudaStream_t st, int32_t* x, int64_t per, const int2* pairs, int npairs);
 // out[b][I][J] = a[b][J][I] * c[b][I][J] for nb blocks of n x n.
 cudaError_t hadamard_t(cudaStream_t st, const double2* a, const double2* c, int n, int nb, double2* out);
 

@@ -59,10 +59,14 @@ struct isdf_handle {
   std::vector<std::pair<std::string, DevBuf>> bufs;
   bool has_points = false, has_fit = false, has_xi = false, has_eta = false, has_coulomb = false;
   std::vector<int32_t> ips;
-  std::vector<int32_t> ranks;
+  std::vector<int32_t> ranks;    // rank r_q of the truncated factor of Pi^q, per q
+  std::vector<int32_t> ranks_v;  // rank n_q of V_xi^q (columns of L^q), per q
+  int xi_rows = 0;               // rows of xi kept per q: max_q r_q (rows beyond r_q are zero)
   std::string err;
   int64_t launches = 0;
   std::vector<int2> tiles_host;
+  std::vector<int> tile_of_host;
+  std::vector<int2> orb_host;
   // device bytes for one q-chunk of the fp16 slices of B (mixed contraction)
   size_t split_budget = (size_t)12 << 30;
   // pair q with -q in the fragment contraction (time-reversal symmetry)
@@ -380,6 +384,8 @@ int coulomb_tail(isdf_handle* h, double2* Vxi, void* V_out) {
   ENSURE(rankV, int32_t, "rankV", nk);
   ENSURE(dwork, double, "chol_dwork", (size_t)nk * 2 * np);
   CK(pchol_batched(h->st, Vxi, np, nk, 1e-15, LtV, permV, rankV, dwork));
+  h->ranks_v.assign(nk, 0);
+  CK(cudaMemcpyAsync(h->ranks_v.data(), rankV, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, h->st));
   ENSURE(Lxi, double2, "W_work", (size_t)nk * np * np);
   CK(lt_to_rowmajor(h->st, LtV, rankV, np, nk, Lxi));
   ENSURE(Lq, double2, "Lq", (size_t)nk * np * np);
@@ -615,30 +621,44 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
   ENSURE(W, double2, "W", (size_t)nk * np * np);
   ENSURE(wwork, double2, "W_work", (size_t)nk * np * np);
   ENSURE(xi, double2, "xi", (size_t)nk * np * ng);
-  const int64_t pp = (int64_t)np * np, pg = (int64_t)np * ng;
-  for (const auto& r : qh.runs) {
-    const int q0 = r.first, nq = r.second;
-    CK(pchol_batched(h->st, Pi + q0 * pp, np, nq, solve_tol, LtPi + q0 * pp, permPi + (int64_t)q0 * np,
-                     rankPi + q0, dwork + (int64_t)q0 * 2 * np));
-    CK(trinv_batched(h->st, LtPi + q0 * pp, permPi + (int64_t)q0 * np, rankPi + q0, np, nq, W + q0 * pp,
-                     wwork + q0 * pp));
-    // xi^q = W eta^q = L_S^{-1} (eta^q rows in pivot order): triangular, gathered
-    CK(ztrmm_gather(h->st, np, ng, wwork + q0 * pp, np, pp, permPi + (int64_t)q0 * np, np, eta + q0 * pg, ng, pg,
-                    xi + q0 * pg, ng, pg, nq));
-  }
+  const int64_t pp = (int64_t)np * np;
+  for (const auto& r : qh.runs)
+    CK(pchol_batched(h->st, Pi + r.first * pp, np, r.second, solve_tol, LtPi + r.first * pp,
+                     permPi + (int64_t)r.first * np, rankPi + r.first, dwork + (int64_t)r.first * 2 * np));
   if (!qh.mirror.empty()) {
     ENSURE(mir, int2, "q_mirror", qh.mirror.size());
     CK(cudaMemcpyAsync(mir, qh.mirror.data(), sizeof(int2) * qh.mirror.size(), cudaMemcpyHostToDevice, h->st));
-    CK(mirror_conj(h->st, W, pp, mir, (int)qh.mirror.size()));
-    CK(mirror_conj(h->st, xi, pg, mir, (int)qh.mirror.size()));
+    // conj(Pi^q) has the diagonals of Pi^q, so the same pivot order and rank
+    CK(mirror_copy(h->st, permPi, np, mir, (int)qh.mirror.size()));
+    CK(mirror_copy(h->st, rankPi, 1, mir, (int)qh.mirror.size()));
   }
   h->ranks.assign(nk, 0);
   CK(cudaMemcpyAsync(h->ranks.data(), rankPi, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
-  for (const int2& m : qh.mirror) h->ranks[m.x] = h->ranks[m.y];
   if (rank_out) std::memcpy(rank_out, h->ranks.data(), sizeof(int32_t) * nk);
   for (int q = 0; q < nk; ++q)
     if (h->ranks[q] < 1) return fail(h, ISDF_ERR_NUMERIC, "Pi^q has rank 0 at q=%d", q);
+  // xi^q = W eta^q has nonzero rows only below r_q: keep r_max rows per q
+  const int rx = *std::max_element(h->ranks.begin(), h->ranks.end());
+  const int64_t pg = (int64_t)np * ng, xg = (int64_t)rx * ng;
+  for (const auto& r : qh.runs) {
+    const int q0 = r.first, nq = r.second;
+    CK(trinv_batched(h->st, LtPi + q0 * pp, permPi + (int64_t)q0 * np, rankPi + q0, np, nq, W + q0 * pp,
+                     wwork + q0 * pp));
+    // xi^q = W eta^q = L_S^{-1} (eta^q rows in pivot order): triangular, gathered
+    CK(ztrmm_gather(h->st, rx, ng, wwork + q0 * pp, np, pp, permPi + (int64_t)q0 * np, np, eta + q0 * pg, ng, pg,
+                    xi + q0 * xg, ng, xg, nq));
+  }
+  if (!qh.mirror.empty()) {
+    const int2* mir = (const int2*)h->buf("q_mirror");
+    CK(mirror_conj(h->st, W, pp, mir, (int)qh.mirror.size()));
+    CK(mirror_conj(h->st, xi, xg, mir, (int)qh.mirror.size()));
+  }
+  h->xi_rows = rx;
+  double tri = 0.0;  // triangular xi = W eta over the computed q: r_q^2 / 2 complex MACs per grid point
+  for (const auto& r : qh.runs)
+    for (int q = r.first; q < r.first + r.second; ++q) tri += (double)h->ranks[q] * h->ranks[q];
+  stt.flops = 8.0 * nk * (double)np * ng * nao + 4.0 * tri * ng;
   h->has_fit = true;
   h->has_xi = true;
   h->has_eta = true;
@@ -658,27 +678,32 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
   const double2* tw = (const double2*)h->buf("grid_tw");
   const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
   const QHalf qh = fit_q_set(km, h->q_sym);
-  StageTimer stt(h, 2, 4.0 * qh.count * (double)np * np * ng);  // Hermitian V_xi GEMM
+  // xi^q has rx = max_q r_q rows (the rest of the rows of W eta^q vanish), so the
+  // grid FFT and the Hermitian GEMM run over rx rows and V_xi is zero beyond them
+  const int rx = h->xi_rows;
+  StageTimer stt(h, 2, 4.0 * qh.count * (double)rx * rx * ng);  // Hermitian V_xi GEMM
   ENSURE(Vxi, double2, "Vxi", (size_t)nk * np * np);
   ENSURE(gwork, uint8_t, "grid_work", grid_coulomb_work_bytes(nk, h->cell));
-  const int64_t pp = (int64_t)np * np, pg = (int64_t)np * ng;
+  const int64_t pp = (int64_t)np * np, xg = (int64_t)rx * ng;
+  CK(cudaMemsetAsync(Vxi, 0, sizeof(double2) * (size_t)nk * pp, h->st));
   if (h->prec == ISDF_FP64) {
     for (const auto& r : qh.runs) {
-      CK(grid_coulomb_fft(h->st, xi + r.first * pg, np, r.first, r.second, h->cell, tw, gwork));
-      CK(zgemm(h->st, 'R', 'T', np, np, ng, make_double2(h->volume, 0.0), xi + r.first * pg, ng, pg,
-               xi + r.first * pg, ng, pg, zero, Vxi + r.first * pp, np, pp, r.second));
+      CK(grid_coulomb_fft(h->st, xi + r.first * xg, rx, r.first, r.second, h->cell, tw, gwork));
+      CK(zgemm(h->st, 'R', 'T', rx, rx, ng, make_double2(h->volume, 0.0), xi + r.first * xg, ng, xg,
+               xi + r.first * xg, ng, xg, zero, Vxi + r.first * pp, np, pp, r.second));
     }
   } else {
     // V_xi in complex64 with compensated accumulation: xi is well scaled (|xi| ~ |rho|), and
     // an error in V_xi reaches E as P dV_xi P^H with P = M W^T well scaled, i.e. relative to
     // |E| (the ill-conditioned factor W is applied afterwards, in FP64).
-    ENSURE(xif, float2, "xi_f", (size_t)nk * np * ng);
+    ENSURE(xif, float2, "xi_f", (size_t)nk * xg);
     ENSURE(Vxif, float2, "Vxi_f", (size_t)nk * np * np);
+    CK(cudaMemsetAsync(Vxif, 0, sizeof(float2) * (size_t)nk * pp, h->st));
     for (const auto& r : qh.runs) {
-      CK(z2c(h->st, xi + r.first * pg, xif + r.first * pg, r.second * pg));
-      CK(grid_coulomb_fft_f(h->st, xif + r.first * pg, np, r.first, r.second, h->cell, tw, gwork));
-      CK(cgemm(h->st, 'R', 'T', np, np, ng, make_float2((float)h->volume, 0.f), xif + r.first * pg, ng, pg,
-               xif + r.first * pg, ng, pg, make_float2(0.f, 0.f), Vxif + r.first * pp, np, pp, r.second));
+      CK(z2c(h->st, xi + r.first * xg, xif + r.first * xg, r.second * xg));
+      CK(grid_coulomb_fft_f(h->st, xif + r.first * xg, rx, r.first, r.second, h->cell, tw, gwork));
+      CK(cgemm(h->st, 'R', 'T', rx, rx, ng, make_float2((float)h->volume, 0.f), xif + r.first * xg, ng, xg,
+               xif + r.first * xg, ng, xg, make_float2(0.f, 0.f), Vxif + r.first * pp, np, pp, r.second));
       CK(c2z(h->st, Vxif + r.first * pp, Vxi + r.first * pp, r.second * pp));
     }
   }
@@ -774,6 +799,20 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
   CK(cudaMemcpyAsync(swd, sw.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, h->st));
   const double2* Lq = (const double2*)h->buf("Lq");
   const int64_t pp = (int64_t)np * np;
+  // Structural zeros of L^q = W^T L_xi: nonzero rows perm_q[c] (c < r_q, the
+  // pivots of Pi^q), nonzero columns J < n_q (the rank of V_xi^q).  B^q = M^q L^q
+  // needs only those; rp and nv bound them over the q of the sum.
+  int rp = 1, nv = 1;
+  double sum_nv = 0.0, sum_rn = 0.0;
+  for (int q : qs) {
+    rp = std::max(rp, (int)h->ranks[q]);
+    nv = std::max(nv, (int)h->ranks_v[q]);
+    sum_nv += h->ranks_v[q];
+    sum_rn += (double)h->ranks[q] * h->ranks_v[q];
+  }
+  const int nj = (int)std::min<int64_t>(np, ((int64_t)nv + 3) / 4 * 4);  // columns of B^q
+  const int32_t* permPi = (const int32_t*)h->buf("permPi");
+  const int32_t* rankPi = (const int32_t*)h->buf("rankPi");
   for (int f = 0; f < n_frag; ++f) {
     const int nf = n_orb[f];
     const int64_t n2 = (int64_t)nf * nf;
@@ -791,7 +830,7 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       ENSURE(Lw, double2, "frag_Lw", (size_t)nk * pp);
       ENSURE(T, double2, "frag_T", (size_t)nk * np * nf);
       ENSURE(M, double2, "frag_M", (size_t)nk * sq);
-      ENSURE(B, double2, "frag_B", (size_t)n2 * nS * np);
+      ENSURE(B, double2, "frag_B", (size_t)n2 * nS * nj);
       ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
       if (f == 0) CK(scale_blocks(h->st, Lq, pp, nk, swd, Lw));
       {
@@ -803,15 +842,16 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         CK(kdft_cols(h->st, M, n2 * np, km, +1, +1, 0, 1.0 / nk));
       }
       {
-        // B = [w_q^{1/2} M^q L^q]_{q in S}, compact: B[a][slot(q) np + J]
-        StageTimer stt(h, 4, 8.0 * (double)n2 * pp * nS);
+        // B = [w_q^{1/2} M^q L^q]_{q in S}, compact: B[a][slot(q) nj + J], the nj
+        // nonzero columns of L^q
+        StageTimer stt(h, 4, 8.0 * (double)n2 * np * sum_nv);
         for (const auto& r : runs)
-          CK(zgemm(h->st, 'N', 'N', (int)n2, np, np, one, M + r.first * sq, np, sq, Lw + r.first * pp, np, pp, zero,
-                   B + (int64_t)slot[r.first] * np, (int64_t)nS * np, np, r.second));
+          CK(zgemm(h->st, 'N', 'N', (int)n2, nj, np, one, M + r.first * sq, np, sq, Lw + r.first * pp, np, pp, zero,
+                   B + (int64_t)slot[r.first] * nj, (int64_t)nS * nj, nj, r.second));
       }
       {
-        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nS * np);
-        CK(zgemm(h->st, 'N', 'C', (int)n2, (int)n2, nS * np, one, B, (int64_t)nS * np, 0, B, (int64_t)nS * np, 0,
+        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * sum_nv);
+        CK(zgemm(h->st, 'N', 'C', (int)n2, (int)n2, nS * nj, one, B, (int64_t)nS * nj, 0, B, (int64_t)nS * nj, 0,
                  zero, E, n2, 0, 1));
         if (h->q_sym) CK(eri_swapconj_sym(h->st, E, nf));
       }
@@ -820,33 +860,37 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     } else {
       const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
       float2* Xf = (float2*)h->buf("X_f");
-      // B = M L on the tensor cores (four exact slices) when 2 N_P fits their exact
-      // accumulation, else on the compensated SIMT GEMM
-      const bool tc_ml = mlgemm_tc_supported(np);
+      // B = M L on the tensor cores (four exact slices) when the 2 r_q gathered
+      // columns fit their exact accumulation, else on the compensated SIMT GEMM
+      const bool tc_ml = mlgemm_tc_supported(rp);
       float2* Lwf = nullptr;
       void* lsl = nullptr;
       int* lexp = nullptr;
       if (tc_ml) {
-        lsl = h->ensure_evict("frag_Lsl", mlgemm_tc_lslice_bytes(nk, np));
-        lexp = (int*)h->ensure_evict("frag_Lexp", sizeof(int) * (size_t)nk * mlgemm_tc_np_pad(np));
+        lsl = h->ensure_evict("frag_Lsl", mlgemm_tc_lslice_bytes(nk, rp, nj));
+        lexp = (int*)h->ensure_evict("frag_Lexp", sizeof(int) * (size_t)nk * mlgemm_tc_nj_pad(nj));
         if (!lsl || !lexp) return fail(h, ISDF_ERR_OOM, "device allocation of the slices of L failed");
       } else {
         Lwf = (float2*)h->ensure_evict("frag_Lwf", sizeof(float2) * (size_t)nk * pp);
         if (!Lwf) return fail(h, ISDF_ERR_OOM, "device allocation of frag_Lwf failed");
       }
       ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nf);
-      ENSURE(T, float2, "frag_Tf", (size_t)nk * np * nf);
+      ENSURE(T, float2, "frag_T", (size_t)nk * np * nf);
       ENSURE(M, float2, "frag_Mf", (size_t)nk * sq);
       ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
       std::vector<int2>& tl = h->tiles_host;
-      herk_tc_tiles(n2, tl);
-      // B^q = w_q^{1/2} M^q L^q overwrites M^q, qc q-points at a time (through Bc on the
-      // SIMT path); the contraction then takes the B^q of S in chunks of qc q-points
-      // (fp16 slices of qc np columns).  qc fits both slice buffers in the workspace limit.
-      const size_t per_q = std::max(herk_tc_split_bytes(n2, np), tc_ml ? mlgemm_tc_split_bytes(n2, np, 1) : 0);
+      syrk_tc_tiles(n2, tl, h->tile_of_host);
+      pair_orbits(nf, h->orb_host);
+      const int norb = (int)h->orb_host.size();
+      // B^q = w_q^{1/2} M^q L^q overwrites M^q (row pitch nj on the tensor-core
+      // path, np through Bc on the SIMT path), qc q-points at a time; E' then
+      // takes the rows of B^q of S in chunks of qc q-points (fp16 slices of
+      // 2 qc nj columns).  qc fits both slice buffers in the workspace limit.
+      const int64_t ldB = tc_ml ? nj : np;
+      const size_t per_q = std::max(syrk_tc_split_bytes(n2, nj), tc_ml ? mlgemm_tc_split_bytes(n2, rp, 1) : 0);
       const int qc = (int)std::max<int64_t>(1, std::min<int64_t>(nS, (int64_t)(h->split_budget / per_q)));
       ENSURE(split, uint8_t, "tc_split",
-             std::max(herk_tc_split_bytes(n2, (int64_t)qc * np), tc_ml ? mlgemm_tc_split_bytes(n2, np, qc) : 0));
+             std::max(syrk_tc_split_bytes(n2, (int64_t)qc * nj), tc_ml ? mlgemm_tc_split_bytes(n2, rp, qc) : 0));
       float2* Bc = nullptr;
       if (!tc_ml) {
         Bc = (float2*)h->ensure_evict("frag_Bc", sizeof(float2) * (size_t)qc * sq);
@@ -854,13 +898,18 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       }
       ENSURE(rexp, int, "tc_rowexp", n2);
       ENSURE(tiles_d, int2, "tc_tiles", tl.size());
-      ENSURE(ws, uint8_t, "tc_ws", herk_tc_ws_bytes((int64_t)tl.size()));
+      ENSURE(tile_of_d, int, "tc_tile_of", h->tile_of_host.size());
+      ENSURE(orb_d, int2, "tc_orbits", norb);
+      ENSURE(ws, uint8_t, "tc_ws", syrk_tc_ws_bytes((int64_t)tl.size()));
       ENSURE(tcw, int, "tc_words", 4);
       CK(cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
+      CK(cudaMemcpyAsync(tile_of_d, h->tile_of_host.data(), h->tile_of_host.size() * sizeof(int),
+                         cudaMemcpyHostToDevice, h->st));
+      CK(cudaMemcpyAsync(orb_d, h->orb_host.data(), norb * sizeof(int2), cudaMemcpyHostToDevice, h->st));
       CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
       if (f == 0) {
         if (tc_ml)
-          CK(mlgemm_tc_prepare(h->st, Lq, swd, nk, np, lsl, lexp));
+          CK(mlgemm_tc_prepare(h->st, Lq, swd, nk, np, permPi, rankPi, rp, nj, lsl, lexp));
         else
           CK(scale_blocks_f(h->st, Lq, pp, nk, swd, Lwf));
       }
@@ -874,13 +923,14 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         CK(kdft_cols_f(h->st, M, n2 * np, km, +1, +1, 0, 1.f / nk));
       }
       {
-        StageTimer stt(h, 4, 8.0 * (double)n2 * pp * nS);
+        StageTimer stt(h, 4, 8.0 * (double)n2 * (tc_ml ? sum_rn : (double)np * sum_nv));
         if (tc_ml) {
-          // row exponents of M over the q of the sum, then B^q = M^q L^q over M^q, q-chunk by q-chunk
-          CK(herk_tc_rowscale(h->st, M, sq, np, np, qmap, n2, (int64_t)nS * np, rexp));
+          // row exponents of the gathered M over the q of the sum, then B^q = M^q L^q
+          // over M^q, q-chunk by q-chunk
+          CK(mlgemm_tc_rowscale(h->st, M, sq, np, qmap, nS, permPi, rankPi, rp, n2, rexp));
           for (int j0 = 0; j0 < nS; j0 += qc)
-            CK(mlgemm_tc_chunk(h->st, M, sq, qmap, n2, np, j0, std::min(qc, nS - j0), rexp, split, lsl, lexp, nk,
-                               tcw + 1));
+            CK(mlgemm_tc_chunk(h->st, M, sq, qmap, n2, np, permPi, rankPi, rp, nj, j0, std::min(qc, nS - j0), rexp,
+                               split, lsl, lexp, nk, tcw + 1));
         } else {
           for (const auto& r : runs)
             for (int q0 = r.first; q0 < r.first + r.second; q0 += qc) {
@@ -893,15 +943,17 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         }
       }
       {
-        StageTimer stt(h, 5, 4.0 * (double)n2 * n2 * nS * np);
-        CK(herk_tc_rowscale(h->st, M, sq, np, np, qmap, n2, (int64_t)nS * np, rexp));
+        // E' = c sum_{q in S} [Re R^q, Im R^q][Re R^q, Im R^q]^T over the rows of B^q in the
+        // time-reversal basis (real symmetric, lower-triangle tiles), then E = W E' W^H;
+        // c = 2 with the pairing (S about half the mesh), 1 over every q
+        StageTimer stt(h, 5, 2.0 * (double)n2 * (double)(n2 + 1) * sum_nv);
+        CK(syrk_tc_rowscale(h->st, M, sq, ldB, nj, qmap, nS, orb_d, nf, rexp));
         for (int j0 = 0; j0 < nS; j0 += qc) {
           const int nq = std::min(qc, nS - j0);
-          CK(herk_tc_chunk(h->st, M, sq, np, np, qmap, n2, (int64_t)j0 * np, (int64_t)nq * np, rexp, split, tiles_d,
-                           (int)tl.size(), ws, j0 > 0, tcw + 1));
+          CK(syrk_tc_chunk(h->st, M, sq, ldB, nj, qmap, orb_d, nf, j0, nq, rexp, split, tiles_d, (int)tl.size(), ws,
+                           j0 > 0, tcw + 1));
         }
-        CK(herk_tc_finish(h->st, ws, tiles_d, (int)tl.size(), n2, rexp, 1.0 / nk, E));
-        if (h->q_sym) CK(eri_swapconj_sym(h->st, E, nf));
+        CK(syrk_tc_finish(h->st, ws, (int)tl.size(), tile_of_d, orb_d, nf, rexp, (h->q_sym ? 2.0 : 1.0) / nk, E));
       }
       if (eri_out && eri_out[f]) CK(eri_permute_zc(h->st, E, nf, 1.0, (float2*)eri_out[f]));
       if (want_tr) CK(eri_traces(h->st, E, nf, 1.0, (const double2*)gamma[f], trf));
@@ -1104,8 +1156,10 @@ int isdf_get(isdf_handle* h, int what, void* out) {
     case 3: {
       if (!h->has_xi) return fail(h, ISDF_ERR_STATE, "zeta not available (needs isdf_fit_zeta, before the metric)");
       const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-      CK(zgemm(h->st, 'C', 'N', np, ng, np, one, (double2*)h->buf("W"), np, (int64_t)np * np, (double2*)h->buf("xi"),
-               ng, (int64_t)np * ng, zero, (double2*)out, ng, (int64_t)np * ng, nk));
+      // zeta = W^H xi with the rx stored rows of xi
+      const int rx = h->xi_rows;
+      CK(zgemm(h->st, 'C', 'N', np, ng, rx, one, (double2*)h->buf("W"), np, (int64_t)np * np, (double2*)h->buf("xi"),
+               ng, (int64_t)rx * ng, zero, (double2*)out, ng, (int64_t)np * ng, nk));
       break;
     }
     default:

@@ -89,11 +89,159 @@ __device__ void kmesh_dft_smem(T* s, int ct, const int n[3], const typename CT<T
   }
 }
 
-// The same for a cubic mesh of compile-time side L: the twiddle indices are
-// compile-time constants, so the L twiddles of the pass live in registers, and
-// ct is a power of two (lct = log2 ct).
+// Small DFTs in registers for a compile-time length N, as a sub-transform of
+// an L-point table: W_N^t = (wc[(t S) mod L], ws[(t S) mod L]) with S = L / N
+// (the table holds exp(+-2 pi i t/L), the sign baked into ws).  Composite N
+// goes by Cooley-Tukey over its smallest prime factor P (N = P Q):
+//   X[k1 + P k2] = sum_n2 W_N^{n2 k1} W_Q^{n2 k2} sum_n1 x[Q n1 + n2] W_P^{n1 k1};
+// N = 2, 3 and 5 are written out with the symmetric pairs (x_j +- x_{N-j})
+// so that each output costs a few real multiplies; other primes fall back to
+// the direct sum.
+constexpr int smallest_factor(int n) {
+  for (int f = 2; f * f <= n; ++f)
+    if (n % f == 0) return f;
+  return n;
+}
+
+template <typename R, int N, int S, int L, int P = smallest_factor(N)>
+struct Dft {
+  __host__ __device__ __forceinline__ static void run(R* xr, R* xi, const R* wc, const R* ws) {
+    constexpr int Q = N / P;
+    R yr[N], yi[N];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+      R ar[P], ai[P];
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) {
+        ar[n1] = xr[Q * n1 + n2];
+        ai[n1] = xi[Q * n1 + n2];
+      }
+      Dft<R, P, S * Q, L>::run(ar, ai, wc, ws);
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) {
+        // twiddle W_N^{n2 k1}
+        const int t = (n2 * k1 * S) % L;
+        if (t == 0) {
+          yr[k1 * Q + n2] = ar[k1];
+          yi[k1 * Q + n2] = ai[k1];
+        } else {
+          yr[k1 * Q + n2] = ar[k1] * wc[t] - ai[k1] * ws[t];
+          yi[k1 * Q + n2] = ar[k1] * ws[t] + ai[k1] * wc[t];
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      R br[Q], bi[Q];
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) {
+        br[n2] = yr[k1 * Q + n2];
+        bi[n2] = yi[k1 * Q + n2];
+      }
+      Dft<R, Q, S * P, L>::run(br, bi, wc, ws);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) {
+        xr[k1 + P * k2] = br[k2];
+        xi[k1 + P * k2] = bi[k2];
+      }
+    }
+  }
+};
+
+// prime N without a written-out form: the direct sum
+template <typename R, int N, int S, int L>
+struct Dft<R, N, S, L, N> {
+  __host__ __device__ __forceinline__ static void run(R* xr, R* xi, const R* wc, const R* ws) {
+    R or_[N], oi[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      R ax = 0, ay = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int t = ((i * j) % N) * S % L;
+        ax += xr[i] * wc[t] - xi[i] * ws[t];
+        ay += xr[i] * ws[t] + xi[i] * wc[t];
+      }
+      or_[j] = ax;
+      oi[j] = ay;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      xr[j] = or_[j];
+      xi[j] = oi[j];
+    }
+  }
+};
+
+template <typename R, int S, int L>
+struct Dft<R, 1, S, L, 1> {
+  __host__ __device__ __forceinline__ static void run(R*, R*, const R*, const R*) {}
+};
+
+template <typename R, int S, int L>
+struct Dft<R, 2, S, L, 2> {
+  __host__ __device__ __forceinline__ static void run(R* xr, R* xi, const R*, const R*) {
+    const R r0 = xr[0], i0 = xi[0];
+    xr[0] = r0 + xr[1];
+    xi[0] = i0 + xi[1];
+    xr[1] = r0 - xr[1];
+    xi[1] = i0 - xi[1];
+  }
+};
+
+// W = W_3^1 = c + i s:  X0 = x0 + a,  X1,2 = x0 + c a +- i s b  with a = x1 + x2, b = x1 - x2
+template <typename R, int S, int L>
+struct Dft<R, 3, S, L, 3> {
+  __host__ __device__ __forceinline__ static void run(R* xr, R* xi, const R* wc, const R* ws) {
+    const R c = wc[S % L], s = ws[S % L];
+    const R ar = xr[1] + xr[2], ai = xi[1] + xi[2], br = xr[1] - xr[2], bi = xi[1] - xi[2];
+    const R tr = xr[0] + c * ar, ti = xi[0] + c * ai;
+    xr[0] += ar;
+    xi[0] += ai;
+    xr[1] = tr - s * bi;
+    xi[1] = ti + s * br;
+    xr[2] = tr + s * bi;
+    xi[2] = ti - s * br;
+  }
+};
+
+// W = W_5^1 = c1 + i s1, W^2 = c2 + i s2; a_j = x_j + x_{5-j}, b_j = x_j - x_{5-j}:
+//   X1,4 = x0 + c1 a1 + c2 a2 +- i (s1 b1 + s2 b2),  X2,3 = x0 + c2 a1 + c1 a2 +- i (s2 b1 - s1 b2)
+template <typename R, int S, int L>
+struct Dft<R, 5, S, L, 5> {
+  __host__ __device__ __forceinline__ static void run(R* xr, R* xi, const R* wc, const R* ws) {
+    const R c1 = wc[S % L], s1 = ws[S % L], c2 = wc[(2 * S) % L], s2 = ws[(2 * S) % L];
+    const R a1r = xr[1] + xr[4], a1i = xi[1] + xi[4], b1r = xr[1] - xr[4], b1i = xi[1] - xi[4];
+    const R a2r = xr[2] + xr[3], a2i = xi[2] + xi[3], b2r = xr[2] - xr[3], b2i = xi[2] - xi[3];
+    const R t1r = xr[0] + c1 * a1r + c2 * a2r, t1i = xi[0] + c1 * a1i + c2 * a2i;
+    const R t2r = xr[0] + c2 * a1r + c1 * a2r, t2i = xi[0] + c2 * a1i + c1 * a2i;
+    const R u1r = s1 * b1r + s2 * b2r, u1i = s1 * b1i + s2 * b2i;  // i u1 = (-u1i, u1r)
+    const R u2r = s2 * b1r - s1 * b2r, u2i = s2 * b1i - s1 * b2i;
+    xr[0] += a1r + a2r;
+    xi[0] += a1i + a2i;
+    xr[1] = t1r - u1i;
+    xi[1] = t1i + u1r;
+    xr[4] = t1r + u1i;
+    xi[4] = t1i - u1r;
+    xr[2] = t2r - u2i;
+    xi[2] = t2i + u2r;
+    xr[3] = t2r + u2i;
+    xi[3] = t2i - u2r;
+  }
+};
+
+// Cubic mesh of compile-time side L: the three per-axis passes in place on
+// s[k][c] (Nk x ct, ct = 2^lct columns), line per thread, with the mixed-radix
+// DFT above in registers.  Element (k, c) sits at (k << lct) + c + (k / L) padk:
+// the padding after each group of L rows shifts the lines that one 128-byte
+// shared-memory phase serves onto different banks (see kdft_cubic_pad).
 template <typename T, int L>
-__device__ void kmesh_dft_cubic(T* s, int lct, const typename CT<T>::R* tcs, const typename CT<T>::R* tss) {
+__device__ __forceinline__ int cidx(int k, int c, int lct, int padk) {
+  return (k << lct) + c + (k / L) * padk;
+}
+
+template <typename T, int L>
+__device__ void kmesh_dft_cubic(T* s, int lct, int padk, const typename CT<T>::R* tcs, const typename CT<T>::R* tss) {
   using R = typename CT<T>::R;
   R wc[L], ws[L];
 #pragma unroll
@@ -110,28 +258,24 @@ __device__ void kmesh_dft_cubic(T* s, int lct, const typename CT<T>::R* tcs, con
       const int rest = line >> lct;
       const int hi = rest / stride, lo = rest % stride;
       const int base = hi * stride * L + lo;
-      T v[L];
+      R vr[L], vi[L];
 #pragma unroll
-      for (int i = 0; i < L; ++i) v[i] = s[((base + i * stride) << lct) + c];
-#pragma unroll
-      for (int j = 0; j < L; ++j) {
-        R ax = 0, ay = 0;
-#pragma unroll
-        for (int i = 0; i < L; ++i) {
-          const int t = (i * j) % L;
-          ax += v[i].x * wc[t] - v[i].y * ws[t];
-          ay += v[i].x * ws[t] + v[i].y * wc[t];
-        }
-        s[((base + j * stride) << lct) + c] = CT<T>::mk(ax, ay);
+      for (int i = 0; i < L; ++i) {
+        const T v = s[cidx<T, L>(base + i * stride, c, lct, padk)];
+        vr[i] = v.x;
+        vi[i] = v.y;
       }
+      Dft<R, L, 1, L>::run(vr, vi, wc, ws);
+#pragma unroll
+      for (int j = 0; j < L; ++j) s[cidx<T, L>(base + j * stride, c, lct, padk)] = CT<T>::mk(vr[j], vi[j]);
     }
     __syncthreads();
   }
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, int64_t ncol, int lct, int mode,
-                                                         Twiddles16 tw1, Twiddles16 tw2, double scale) {
+__global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, int64_t ncol, int lct, int padk,
+                                                         int mode, Twiddles16 tw1, Twiddles16 tw2, double scale) {
   using R = typename CT<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
@@ -150,26 +294,40 @@ __global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, i
     const int64_t col = c0 + c;
     T v = CT<T>::mk(0, 0);
     if (col < ncol) v = data[(int64_t)k * ncol + col];
-    s[e] = v;
+    s[cidx<T, L>(k, c, lct, padk)] = v;
   }
   __syncthreads();
-  kmesh_dft_cubic<T, L>(s, lct, tw1c, tw1s);
+  kmesh_dft_cubic<T, L>(s, lct, padk, tw1c, tw1s);
   if (mode == 1) {
     for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
-      T v = s[e];
-      s[e] = CT<T>::mk(v.x * v.x + v.y * v.y, 0);
+      const int i = cidx<T, L>(e >> lct, e & (ct - 1), lct, padk);
+      const T v = s[i];
+      s[i] = CT<T>::mk(v.x * v.x + v.y * v.y, 0);
     }
     __syncthreads();
-    kmesh_dft_cubic<T, L>(s, lct, tw2c, tw2s);
+    kmesh_dft_cubic<T, L>(s, lct, padk, tw2c, tw2s);
   }
   for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
     const int k = e >> lct, c = e & (ct - 1);
     const int64_t col = c0 + c;
     if (col < ncol) {
-      T v = s[e];
+      const T v = s[cidx<T, L>(k, c, lct, padk)];
       data[(int64_t)k * ncol + col] = CT<T>::mk(v.x * (R)scale, v.y * (R)scale);
     }
   }
+}
+
+// Row padding of the cubic k-DFT's shared layout.  One 128-byte phase of a
+// shared access serves G = 128 / sizeof(T) lanes; with ct < G columns per row
+// those lanes span G / ct lines.  Along the stride-1 axis consecutive lines
+// start L rows apart, so they land on the same banks unless the L-row group is
+// padded: padk = (ct - L ct) mod G makes the line offset ct (mod G), i.e. the
+// lanes of a phase cover G consecutive elements.  The other two axes step the
+// line start by one row (ct elements) already.
+inline int kdft_cubic_pad(int L, int ct, int elem) {
+  const int G = 128 / elem;
+  if (ct >= G) return 0;
+  return (((ct - L * ct) % G) + G) % G;
 }
 
 template <typename T, int L>
@@ -178,7 +336,8 @@ cudaError_t kdft_cubic_launch(cudaStream_t st, T* data, int64_t ncol, int mode, 
   constexpr int nk = L * L * L;
   int lct = 0;
   while (lct < 5 && ((int64_t)nk * sizeof(T) << (lct + 1)) <= 65536) ++lct;
-  const size_t smem = (size_t)nk * sizeof(T) << lct;
+  const int padk = kdft_cubic_pad(L, 1 << lct, (int)sizeof(T));
+  const size_t smem = ((size_t)nk << lct) * sizeof(T) + (size_t)(nk / L) * padk * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kdft_cubic_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -186,7 +345,7 @@ cudaError_t kdft_cubic_launch(cudaStream_t st, T* data, int64_t ncol, int mode, 
   }
   const int64_t nblk = (ncol + (1 << lct) - 1) >> lct;
   if (nblk > 2147483647LL) return cudaErrorInvalidValue;
-  kdft_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, lct, mode, t1, t2, scale);
+  kdft_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, lct, padk, mode, t1, t2, scale);
   count_launch();
   return cudaGetLastError();
 }

@@ -1,18 +1,29 @@
 // Tensor-core (tcgen05) kernels of the fragment ERIs, Eq. 19:
 //     E = sum_q B^q B^q^H   with  B^q = M^q L^q   (V^q = L^q L^q^H).
-// herk_tc_kernel forms E (below); mlgemm_tc_kernel forms B (further down, with
+// syrk_tc_kernel forms E (below); mlgemm_tc_kernel forms B (further down, with
 // four slices instead of three).
 //
-// Complex -> real: with B stored as interleaved (re, im) pairs, the real row
-// P_a = (Re B_a0, Im B_a0, Re B_a1, ...) and Q_a = interleaved(-i B_a) give
-//     Re E_ab = P_a . P_b      Im E_ab = Q_a . P_b,
-// so one real GEMM D = A' B'^T with A' rows (P_0, Q_0, P_1, Q_1, ...) and
-// B' = the P rows (every other row of A') yields both parts.  Only tiles that
-// touch the lower triangle of the Hermitian E are computed.
+// Structural zeros of L^q.  Pi^q is factorised with truncation to rank r_q
+// (pivots perm_q[0..r_q)), W = L_S^{-1} is nonzero only in the columns
+// perm_q[c], and V_xi = L_xi L_xi^H has rank n_q <= r_q, so L^q = W^T L_xi is
+// nonzero only in the rows perm_q[c], c < r_q, and the columns J < n_q.
+// B^q = M^q L^q therefore contracts over the r_q gathered columns of M^q and
+// has n_J = max_q n_q columns; nothing else of L^q is touched.
+//
+// E as a real symmetric matrix.  The AO basis is real and the k-mesh
+// Gamma-centred, so V^{-q} = conj(V^q) and M^{-q}_{(qp)} = conj(M^q_{(pq)}), hence
+// E_{s(a) s(b)} = conj(E_ab) with s((pq)) = (qp).  That antiunitary symmetry fixes
+// the basis  u_(pq) = e_(pq) + e_(qp),  v_(pq) = i (e_(pq) - e_(qp))  (p < q)  and
+// e_(pp), so E is real in it.  With the rows of B^q taken in that basis,
+//     R_u = B_(pq) + B_(qp),   R_v = -i (B_(pq) - B_(qp)),   R_pp = B_(pp),
+// E' = sum_{all q} R^q R^q^H is real, i.e. E' = c sum_{q in S} [Re R^q, Im R^q] [Re R^q, Im R^q]^T
+// (c = 2 over the half set S of the time-reversal pairing, c = 1 over every q).
+// One real SYRK of n_f^2 rows replaces the complex HERK: half its real
+// products.  Only lower-triangle tiles are formed; the finish maps E' to E.
 //
 // Precision (error-free slicing after Ozaki, Ogita, Oishi & Rump, 2012): each
-// complex row a is scaled by a power of two 2^e_a so that its largest real
-// component lies in [64, 128), and every scaled value is written as
+// real row is scaled by a power of two 2^e so that its largest entry lies in
+// [64, 128), and every scaled value is written as
 //     v = s1 + s2/128 + s3/128^2 (+ remainder below 2^-15),  s_i integers, |s1| <= 128, |s2|, |s3| <= 64,
 // stored as fp16 (exact).  The tcgen05.mma kind::f16 products of integer
 // slices are integers, and the three weight groups
@@ -25,7 +36,7 @@
 // (TwoSum) accumulator in global memory.  g1 and g2 carry weights 2^-7 and
 // 2^-14, so the truncation of tcgen05's FP32 accumulation over longer runs
 // enters only scaled down: they are drained every 4 and 16 chunks (bias below
-// 1e-7 of |B_a||B_b|).  The result is accurate to ~2^-22 of |B_a||B_b|.
+// 1e-7 of |R_a||R_b|).  The result is accurate to ~2^-22 of |R_a||R_b|.
 //
 // Kernel roles (192 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
 // and issues the MMAs, warps 2-5 drain TMEM into the float-float workspace.
@@ -157,7 +168,7 @@ struct TileArgs {
 };
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    herk_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
+    syrk_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
                    const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mB1,
                    const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, TileArgs args) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -355,98 +366,181 @@ struct BView {
   }
 };
 
-// Per complex row a: exponent e_a with max_k max(|Re B_ak|, |Im B_ak|) 2^e_a in [64, 128).
-__global__ void row_scale_kernel(BView B, int64_t n2, int64_t K, int* __restrict__ row_exp) {
-  const int64_t a = blockIdx.x;
-  if (a >= n2) return;
-  float m = 0.f;
+__device__ __forceinline__ float amax2(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+// Exponent e with m 2^e in [64, 128) (0 for a zero or non-finite maximum).
+__device__ __forceinline__ int slice_exp(float m) { return (m > 0.f && isfinite(m)) ? 6 - ilogbf(m) : 0; }
+
+// Orbits of the swap (pq) <-> (qp): orb[o] = (p, q); o < P = n_f (n_f - 1)/2 are
+// the pairs p < q in lexicographic order, o = P + p the diagonal (p, p).  Rows
+// of R: pair o -> 2o (u) and 2o + 1 (v); diagonal p -> 2P + p.
+// u and v of a pair from x = B_(pq), y = B_(qp): u = x + y, v = -i (x - y).
+__device__ __forceinline__ float2 pair_u(float2 x, float2 y) { return make_float2(x.x + y.x, x.y + y.y); }
+__device__ __forceinline__ float2 pair_v(float2 x, float2 y) { return make_float2(x.y - y.y, y.x - x.x); }
+
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* sm) {
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T m = sm[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = max(m, sm[i]);
+  __syncthreads();
+  return m;
+}
+
+// Row exponents of R over the whole sum (one block per orbit).
+__global__ void rrow_scale_kernel(BView B, const int2* __restrict__ orb, int nf, int64_t K,
+                                  int* __restrict__ row_exp) {
+  const int o = blockIdx.x, P = nf * (nf - 1) / 2;
+  const int2 pq = orb[o];
+  const int64_t a1 = (int64_t)pq.x * nf + pq.y, a2 = (int64_t)pq.y * nf + pq.x;
+  float mu = 0.f, mv = 0.f;
   for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-    const float2 v = B.at(a, k);
-    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    const float2 x = B.at(a1, k);
+    if (o < P) {
+      const float2 y = B.at(a2, k);
+      mu = fmaxf(mu, amax2(pair_u(x, y)));
+      mv = fmaxf(mv, amax2(pair_v(x, y)));
+    } else {
+      mu = fmaxf(mu, amax2(x));
+    }
   }
   __shared__ float sm[32];
-  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
-  __syncthreads();
+  mu = block_max(mu, sm);
+  mv = block_max(mv, sm);
   if (threadIdx.x == 0) {
-    float mm = 0.f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmaxf(mm, sm[i]);
-    row_exp[a] = (mm > 0.f && isfinite(mm)) ? 6 - ilogbf(mm) : 0;
-  }
-}
-
-// Slices of A': row 2a = P_a (Re, Im interleaved), row 2a+1 = Q_a (Im, -Re); columns
-// beyond 2K are zero.  v = x 2^e_a = s1 + s2/128 + s3/128^2 (+ remainder).
-__global__ void split_kernel(BView B, int64_t n2, int64_t k0, int64_t K, int64_t K2,
-                             const int* __restrict__ row_exp, __half* __restrict__ S1, __half* __restrict__ S2,
-                             __half* __restrict__ S3) {
-  const int64_t total = n2 * (K2 / 2);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = e / (K2 / 2), k = e % (K2 / 2);
-    float2 v = make_float2(0.f, 0.f);
-    if (k < K) v = B.at(a, k0 + k);
-    const int ex = row_exp[a];
-    const float pr = ldexpf(v.x, ex), pi = ldexpf(v.y, ex);
-    const float vals[4] = {pr, pi, pi, -pr};
-    __half h1[4], h2[4], h3[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float s1 = rintf(vals[t]);
-      const float r1 = (vals[t] - s1) * 128.f;
-      const float s2 = rintf(r1);
-      const float r2 = (r1 - s2) * 128.f;
-      const float s3 = rintf(r2);
-      h1[t] = __float2half_rn(s1);
-      h2[t] = __float2half_rn(s2);
-      h3[t] = __float2half_rn(s3);
+    if (o < P) {
+      row_exp[2 * o] = slice_exp(mu);
+      row_exp[2 * o + 1] = slice_exp(mv);
+    } else {
+      row_exp[2 * P + (o - P)] = slice_exp(mu);
     }
-    const int64_t rP = (2 * a) * K2 + 2 * k, rQ = (2 * a + 1) * K2 + 2 * k;
-    *reinterpret_cast<__half2*>(S1 + rP) = __halves2half2(h1[0], h1[1]);
-    *reinterpret_cast<__half2*>(S2 + rP) = __halves2half2(h2[0], h2[1]);
-    *reinterpret_cast<__half2*>(S3 + rP) = __halves2half2(h3[0], h3[1]);
-    *reinterpret_cast<__half2*>(S1 + rQ) = __halves2half2(h1[2], h1[3]);
-    *reinterpret_cast<__half2*>(S2 + rQ) = __halves2half2(h2[2], h2[3]);
-    *reinterpret_cast<__half2*>(S3 + rQ) = __halves2half2(h3[2], h3[3]);
   }
 }
 
-// E (complex128, n2 x n2, Hermitian) from the float-float tile workspace,
-// scaled by scale * 2^-(e_a + e_b).
-__global__ void herk_finish_kernel(const float* __restrict__ wh, const float* __restrict__ wl,
-                                   const int2* __restrict__ tiles, int ntiles, int64_t n2,
-                                   const int* __restrict__ row_exp, double scale, double2* __restrict__ E) {
-  const int64_t per = (int64_t)BN * (BM / 2);
-  const int64_t total = per * ntiles;
+// Three integer slices of the (re, im) pair v 2^ex, written as half2 at S_i[at].
+__device__ __forceinline__ void put3(float2 v, int ex, int64_t at, __half* __restrict__ S1, __half* __restrict__ S2,
+                                     __half* __restrict__ S3) {
+  const float vals[2] = {ldexpf(v.x, ex), ldexpf(v.y, ex)};
+  __half h1[2], h2[2], h3[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float s1 = rintf(vals[t]);
+    const float r1 = (vals[t] - s1) * 128.f;
+    const float s2 = rintf(r1);
+    const float r2 = (r1 - s2) * 128.f;
+    const float s3 = rintf(r2);
+    h1[t] = __float2half_rn(s1);
+    h2[t] = __float2half_rn(s2);
+    h3[t] = __float2half_rn(s3);
+  }
+  *reinterpret_cast<__half2*>(S1 + at) = __halves2half2(h1[0], h1[1]);
+  *reinterpret_cast<__half2*>(S2 + at) = __halves2half2(h2[0], h2[1]);
+  *reinterpret_cast<__half2*>(S3 + at) = __halves2half2(h3[0], h3[1]);
+}
+
+// Slices of the R rows for the sum positions j0 .. j0 + nq - 1: row rho holds,
+// at columns 2 (jl nJ + J) and + 1, the (re, im) of R at (position j0 + jl, J);
+// columns beyond 2 nq nJ (up to the padded width K2) are zero.
+__global__ void rsplit_kernel(BView B, const int2* __restrict__ orb, int nf, int64_t j0, int nq, int64_t K2,
+                              const int* __restrict__ row_exp, __half* __restrict__ S1, __half* __restrict__ S2,
+                              __half* __restrict__ S3) {
+  const int no = nf * (nf + 1) / 2, P = nf * (nf - 1) / 2;
+  const int64_t half = K2 / 2, ncol = (int64_t)nq * B.nJ, total = (int64_t)no * half;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(e / per);
-    const int c = (int)((e % per) / (BM / 2));
-    const int al = (int)(e % (BM / 2));
-    const int64_t a = (int64_t)tiles[t].x * (BM / 2) + al;
-    const int64_t b = (int64_t)tiles[t].y * BN + c;
-    if (a >= n2 || b >= n2 || a < b) continue;
-    const size_t base = ((size_t)t * BN + c) * BM;
-    const double f = ldexp(scale, -(row_exp[a] + row_exp[b]));
-    const double re = ((double)wh[base + 2 * al] + (double)wl[base + 2 * al]) * f;
-    const double im = ((double)wh[base + 2 * al + 1] + (double)wl[base + 2 * al + 1]) * f;
-    E[a * n2 + b] = make_double2(re, im);
-    if (a != b) E[b * n2 + a] = make_double2(re, -im);
+    const int o = (int)(e / half);
+    const int64_t c2 = e - (int64_t)o * half;
+    const int2 pq = orb[o];
+    const int64_t a1 = (int64_t)pq.x * nf + pq.y, a2 = (int64_t)pq.y * nf + pq.x;
+    float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+    if (c2 < ncol) {
+      const int64_t k = j0 * B.nJ + c2;
+      x = B.at(a1, k);
+      if (o < P) y = B.at(a2, k);
+    }
+    if (o < P) {
+      put3(pair_u(x, y), row_exp[2 * o], (int64_t)(2 * o) * K2 + 2 * c2, S1, S2, S3);
+      put3(pair_v(x, y), row_exp[2 * o + 1], (int64_t)(2 * o + 1) * K2 + 2 * c2, S1, S2, S3);
+    } else {
+      const int64_t row = 2 * (int64_t)P + (o - P);
+      put3(x, row_exp[row], row * K2 + 2 * c2, S1, S2, S3);
+    }
+  }
+}
+
+// E'(i, j) (symmetric) from the float-float tile workspace of the lower triangle.
+__device__ __forceinline__ double ep_val(const float* __restrict__ wh, const float* __restrict__ wl,
+                                         const int* __restrict__ tile_of, int nt, int64_t i, int64_t j,
+                                         const int* __restrict__ row_exp, double scale) {
+  if (i < j) {
+    const int64_t t = i;
+    i = j;
+    j = t;
+  }
+  const int t = tile_of[(i / BM) * nt + (j / BN)];
+  const size_t base = ((size_t)t * BN + (size_t)(j % BN)) * BM + (size_t)(i % BM);
+  return ((double)wh[base] + (double)wl[base]) * ldexp(scale, -(row_exp[i] + row_exp[j]));
+}
+
+// E (complex128 n2 x n2, full) from E' = W^H E W: E = W E' W^H with the
+// unnormalised rows above, i.e. coefficients 1/2 (u) and +-i/2 (v) for pair
+// rows and 1 for diagonal rows.  One thread per orbit pair writes its 1, 2 or 4 entries.
+__global__ void syrk_finish_kernel(const float* __restrict__ wh, const float* __restrict__ wl,
+                                   const int* __restrict__ tile_of, int nt, const int2* __restrict__ orb, int nf,
+                                   const int* __restrict__ row_exp, double scale, double2* __restrict__ E) {
+  const int no = nf * (nf + 1) / 2, P = nf * (nf - 1) / 2;
+  const int64_t n2 = (int64_t)nf * nf, total = (int64_t)no * no;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int o1 = (int)(e / no), o2 = (int)(e % no);
+    const int2 x1 = orb[o1], x2 = orb[o2];
+    const int64_t a = (int64_t)x1.x * nf + x1.y, as = (int64_t)x1.y * nf + x1.x;
+    const int64_t b = (int64_t)x2.x * nf + x2.y, bs = (int64_t)x2.y * nf + x2.x;
+    if (o1 < P && o2 < P) {
+      const int64_t iu = 2 * (int64_t)o1, ju = 2 * (int64_t)o2;
+      const double U = ep_val(wh, wl, tile_of, nt, iu, ju, row_exp, scale);
+      const double X = ep_val(wh, wl, tile_of, nt, iu, ju + 1, row_exp, scale);
+      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, ju, row_exp, scale);
+      const double Z = ep_val(wh, wl, tile_of, nt, iu + 1, ju + 1, row_exp, scale);
+      E[a * n2 + b] = make_double2(0.25 * (U + Z), 0.25 * (Y - X));
+      E[a * n2 + bs] = make_double2(0.25 * (U - Z), 0.25 * (X + Y));
+      E[as * n2 + b] = make_double2(0.25 * (U - Z), -0.25 * (X + Y));
+      E[as * n2 + bs] = make_double2(0.25 * (U + Z), 0.25 * (X - Y));
+    } else if (o1 < P) {
+      const int64_t iu = 2 * (int64_t)o1, j = 2 * (int64_t)P + (o2 - P);
+      const double U = ep_val(wh, wl, tile_of, nt, iu, j, row_exp, scale);
+      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, j, row_exp, scale);
+      E[a * n2 + b] = make_double2(0.5 * U, 0.5 * Y);
+      E[as * n2 + b] = make_double2(0.5 * U, -0.5 * Y);
+    } else if (o2 < P) {
+      const int64_t i = 2 * (int64_t)P + (o1 - P), ju = 2 * (int64_t)o2;
+      const double U = ep_val(wh, wl, tile_of, nt, i, ju, row_exp, scale);
+      const double X = ep_val(wh, wl, tile_of, nt, i, ju + 1, row_exp, scale);
+      E[a * n2 + b] = make_double2(0.5 * U, -0.5 * X);
+      E[a * n2 + bs] = make_double2(0.5 * U, 0.5 * X);
+    } else {
+      const int64_t i = 2 * (int64_t)P + (o1 - P), j = 2 * (int64_t)P + (o2 - P);
+      E[a * n2 + b] = make_double2(ep_val(wh, wl, tile_of, nt, i, j, row_exp, scale), 0.0);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // B^q = M^q L^q on the tensor cores with four exact slices.
 //
-// Real form: A' rows P_a = (Re M_aI, Im M_aI)_I and Q_a = interleaved(-i M_a),
-// B' rows R_J = (Re L_IJ, -Im L_IJ)_I, so (A' R_J)[P_a] = Re B_aJ and
-// (A' R_J)[Q_a] = Im B_aJ.  M rows are scaled by 2^e_a (largest component of
-// M_a over the q of the sum in [64, 128)), L columns by 2^f_qJ per q; both are
-// cut into four integer slices v = s1 + s2/128 + s3/128^2 + s4/128^3 (28 bits:
-// B = M W^T L_xi carries the cancellation of the ill-conditioned W, and three
-// slices, 21 bits, measurably degrade the traces).  Ten fp16 products feed four
-// weight groups
+// Only the structural nonzeros of L^q enter (see the top of the file): the
+// contraction runs over c < r_q with M^q's column perm_q[c] and L^q's row
+// perm_q[c], and the output has n_J columns.  Real form: A' rows
+// P_a = (Re M_a,perm(c), Im M_a,perm(c))_c and Q_a = interleaved(-i M_a,perm(c)),
+// B' rows R_J = (Re L_perm(c)J, -Im L_perm(c)J)_c, so (A' R_J)[P_a] = Re B_aJ and
+// (A' R_J)[Q_a] = Im B_aJ.  M rows are scaled by 2^e_a (largest gathered
+// component over the q of the sum in [64, 128)), L columns by 2^f_qJ per q; both
+// are cut into four integer slices v = s1 + s2/128 + s3/128^2 + s4/128^3
+// (28 bits: B = M W^T L_xi carries the cancellation of the ill-conditioned W,
+// and three slices, 21 bits, measurably degrade the traces).  Ten fp16
+// products feed four weight groups
 //   g0 = S1T1, g1 = S1T2 + S2T1, g2 = S1T3 + S2T2 + S3T1,
 //   g3 = S1T4 + S2T3 + S3T2 + S4T1;
-// with K' = 2 N_P <= kMlMaxK every partial sum of each group is an integer of
+// with K' = 2 r <= kMlMaxK every partial sum of each group is an integer of
 // magnitude below 2^24 (g3: at most 3 * 2^13 per k), so the FP32 TMEM
 // accumulation is exact; the epilogue forms g0 + g1/2^7 + g2/2^14 + g3/2^21
 // once and rescales.
@@ -458,12 +552,12 @@ constexpr int kMlMaxK = 640;                               // K' bound for exact
 constexpr uint32_t kIdescMl = (1u << 4) | ((uint32_t)(MBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 struct MlArgs {
-  float2* out;          // B: element (a, J) of the chunk's q-point ql at out[slot sq + a np + J]
+  float2* out;          // B: element (a, J) of the chunk's q-point ql at out[slot sq + a nj + J]
   const int* qmap;      // slot of the chunk's q-points (indexed j0 + ql)
   const int* row_exp;   // e_a, [n2]
-  const int* col_exp;   // f_qJ, [Nk][np_pad] indexed by slot
+  const int* col_exp;   // f_qJ, [Nk][nj_pad] indexed by slot
   int64_t sq;           // q stride of out
-  int n2, np, np_pad, j0, nkb;
+  int n2, nj, nj_pad, j0, nkb;
   int* err;
 };
 
@@ -511,7 +605,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       const CUtensorMap* ma[MSL] = {&mA1, &mA2, &mA3, &mA4};
       const CUtensorMap* mb[MSL] = {&mB1, &mB2, &mB3, &mB4};
-      const int arow = ql * 2 * args.n2 + ti * BM, brow = slot * args.np_pad + tj * MBN;
+      const int arow = ql * 2 * args.n2 + ti * BM, brow = slot * args.nj_pad + tj * MBN;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
         if (!mbar_wait(&empty[s], (r & 1) ^ 1, s_err, args.err, 11)) break;
@@ -576,7 +670,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr int kPitch = 2 * MBN + 2;     // floats per staged row (bank-conflict padding)
     float* tileS = reinterpret_cast<float*>(smem);
     const int ea = (okw && a < args.n2) ? args.row_exp[a] : 0;
-    const int* fcol = args.col_exp + (int64_t)slot * args.np_pad + tj * MBN;
+    const int* fcol = args.col_exp + (int64_t)slot * args.nj_pad + tj * MBN;
 #pragma unroll 1
     for (int cb = 0; cb < MBN / 32; ++cb) {
       uint32_t v0[32] = {}, v1[32] = {}, v2[32] = {}, v3[32] = {};
@@ -604,8 +698,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int ar = idx / MBN, Jl = idx % MBN;
         const int64_t aa = (int64_t)ti * (BM / 2) + ar;
         const int J = tj * MBN + Jl;
-        if (aa < args.n2 && J < args.np)
-          outq[aa * args.np + J] = *reinterpret_cast<const float2*>(tileS + ar * kPitch + 2 * Jl);
+        if (aa < args.n2 && J < args.nj)
+          outq[aa * args.nj + J] = *reinterpret_cast<const float2*>(tileS + ar * kPitch + 2 * Jl);
       }
     }
   }
@@ -636,24 +730,44 @@ __device__ __forceinline__ void slice4(R v, __half& h1, __half& h2, __half& h3, 
   h4 = __float2half_rn((float)round_int(r3));
 }
 
+// Row exponents of M over the gathered columns of the q-points of the sum:
+// max over positions Q < nS and c < r_q of |M^{q}_{a, perm_q[c]}|, q = qmap[Q].
+__global__ void mrow_scale_kernel(const float2* __restrict__ M, int64_t sq, int np, const int* __restrict__ qmap,
+                                  int nS, const int* __restrict__ perm, const int* __restrict__ rank, int rp,
+                                  int* __restrict__ row_exp) {
+  const int64_t a = blockIdx.x;
+  float m = 0.f;
+  for (int64_t k = threadIdx.x; k < (int64_t)nS * rp; k += blockDim.x) {
+    const int Q = (int)(k / rp), c = (int)(k % rp);
+    const int q = qmap[Q];
+    if (c < rank[q]) m = fmaxf(m, amax2(M[(int64_t)q * sq + a * np + perm[(int64_t)q * np + c]]));
+  }
+  __shared__ float sm[32];
+  m = block_max(m, sm);
+  if (threadIdx.x == 0) row_exp[a] = slice_exp(m);
+}
+
 // A' slices of M for the q-points j0..j0+nq-1 of the sum: block ql holds rows
-// 2a (P_a) and 2a+1 (Q_a) over Kp columns, zero beyond 2 np.
-__global__ void msplit_kernel(BView M, int64_t n2, int np, int j0, int nq, int Kp, const int* __restrict__ row_exp,
-                              __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3,
-                              __half* __restrict__ S4) {
+// 2a (P_a) and 2a+1 (Q_a) over Kp columns: the gathered columns perm_q[c],
+// c < r_q, zero beyond.
+__global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, const int* __restrict__ qmap,
+                              const int* __restrict__ perm, const int* __restrict__ rank, int64_t n2, int j0, int nq,
+                              int Kp, const int* __restrict__ row_exp, __half* __restrict__ S1,
+                              __half* __restrict__ S2, __half* __restrict__ S3, __half* __restrict__ S4) {
   const int64_t half = Kp / 2, total = (int64_t)nq * n2 * half;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t ql = e / (n2 * half), rem = e % (n2 * half);
-    const int64_t a = rem / half, k = rem % half;
+    const int64_t a = rem / half, c = rem % half;
+    const int q = qmap[j0 + ql];
     float2 v = make_float2(0.f, 0.f);
-    if (k < np) v = M.at(a, (int64_t)(j0 + ql) * np + k);
+    if (c < rank[q]) v = M[(int64_t)q * sq + a * np + perm[(int64_t)q * np + c]];
     const int ex = row_exp[a];
     const float pr = ldexpf(v.x, ex), pi = ldexpf(v.y, ex);
     const float vals[4] = {pr, pi, pi, -pr};
     __half h1[4], h2[4], h3[4], h4[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) slice4<float>(vals[t], h1[t], h2[t], h3[t], h4[t]);
-    const int64_t rP = (ql * 2 * n2 + 2 * a) * Kp + 2 * k, rQ = rP + Kp;
+    const int64_t rP = (ql * 2 * n2 + 2 * a) * Kp + 2 * c, rQ = rP + Kp;
     *reinterpret_cast<__half2*>(S1 + rP) = __halves2half2(h1[0], h1[1]);
     *reinterpret_cast<__half2*>(S2 + rP) = __halves2half2(h2[0], h2[1]);
     *reinterpret_cast<__half2*>(S3 + rP) = __halves2half2(h3[0], h3[1]);
@@ -665,49 +779,44 @@ __global__ void msplit_kernel(BView M, int64_t n2, int np, int j0, int nq, int K
   }
 }
 
-// B' slices of w_q^{1/2} L^q: block (q, J) is the row R_J = (Re L_IJ, -Im L_IJ)_I
-// scaled by 2^f_qJ (largest component in [64, 128)), rows J >= np and columns
-// beyond 2 np zero.  Layout [q][np_pad][Kp] per slice; exponents [q][np_pad].
-__global__ void lslice_kernel(const double2* __restrict__ L, const double* __restrict__ sw, int np, int np_pad,
-                              int Kp, __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3,
+// B' slices of w_q^{1/2} L^q: block (J, q) is the row R_J = (Re L_perm(c)J, -Im L_perm(c)J)_c
+// scaled by 2^f_qJ (largest component in [64, 128)); rows J >= nj, columns
+// c >= r_q and columns beyond 2 r_q are zero.  Layout [q][nj_pad][Kp] per
+// slice; exponents [q][nj_pad].
+__global__ void lslice_kernel(const double2* __restrict__ L, const double* __restrict__ sw, int np,
+                              const int* __restrict__ perm, const int* __restrict__ rank, int nj, int nj_pad, int Kp,
+                              __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3,
                               __half* __restrict__ S4, int* __restrict__ col_exp) {
   const int q = blockIdx.y, J = blockIdx.x;
   const double w = sw[q];
+  const int r = rank[q];
   const double2* Lq = L + (int64_t)q * np * np;
+  const int* pq = perm + (int64_t)q * np;
   double m = 0.0;
-  if (J < np)
-    for (int I = threadIdx.x; I < np; I += blockDim.x) {
-      const double2 v = Lq[(int64_t)I * np + J];
+  if (J < nj)
+    for (int c = threadIdx.x; c < r; c += blockDim.x) {
+      const double2 v = Lq[(int64_t)pq[c] * np + J];
       m = fmax(m, fmax(fabs(v.x * w), fabs(v.y * w)));
     }
   __shared__ double sm[32];
-  __shared__ int s_e;
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mm = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmax(mm, sm[i]);
-    s_e = (mm > 0.0 && isfinite(mm)) ? 6 - ilogb(mm) : 0;
-    col_exp[(int64_t)q * np_pad + J] = s_e;
-  }
-  __syncthreads();
-  const int ex = s_e;
-  const int64_t row = ((int64_t)q * np_pad + J) * Kp;
-  for (int k = threadIdx.x; k < Kp / 2; k += blockDim.x) {
+  m = block_max(m, sm);
+  const int ex = (m > 0.0 && isfinite(m)) ? 6 - ilogb(m) : 0;
+  if (threadIdx.x == 0) col_exp[(int64_t)q * nj_pad + J] = ex;
+  const int64_t row = ((int64_t)q * nj_pad + J) * Kp;
+  for (int c = threadIdx.x; c < Kp / 2; c += blockDim.x) {
     double re = 0.0, im = 0.0;
-    if (J < np && k < np) {
-      const double2 v = Lq[(int64_t)k * np + J];
+    if (J < nj && c < r) {
+      const double2 v = Lq[(int64_t)pq[c] * np + J];
       re = ldexp(v.x * w, ex);
       im = -ldexp(v.y * w, ex);
     }
     __half a1, a2, a3, a4, b1, b2, b3, b4;
     slice4<double>(re, a1, a2, a3, a4);
     slice4<double>(im, b1, b2, b3, b4);
-    *reinterpret_cast<__half2*>(S1 + row + 2 * k) = __halves2half2(a1, b1);
-    *reinterpret_cast<__half2*>(S2 + row + 2 * k) = __halves2half2(a2, b2);
-    *reinterpret_cast<__half2*>(S3 + row + 2 * k) = __halves2half2(a3, b3);
-    *reinterpret_cast<__half2*>(S4 + row + 2 * k) = __halves2half2(a4, b4);
+    *reinterpret_cast<__half2*>(S1 + row + 2 * c) = __halves2half2(a1, b1);
+    *reinterpret_cast<__half2*>(S2 + row + 2 * c) = __halves2half2(a2, b2);
+    *reinterpret_cast<__half2*>(S3 + row + 2 * c) = __halves2half2(a3, b3);
+    *reinterpret_cast<__half2*>(S4 + row + 2 * c) = __halves2half2(a4, b4);
   }
 }
 
@@ -748,137 +857,145 @@ inline int nblk(int64_t total) {
   return nb < 1 ? 1 : (int)nb;
 }
 
+inline int64_t round_up(int64_t x, int64_t m) { return ((x + m - 1) / m) * m; }
+
 }  // namespace tc
 
-size_t herk_tc_split_bytes(int64_t n2, int64_t K) {
-  const int64_t K2 = ((2 * K + tc::BK - 1) / tc::BK) * tc::BK;
-  return (size_t)tc::NSLICE * (2 * n2) * K2 * sizeof(__half) + 256;
+// ---- E = sum_q B^q B^q^H in the real symmetric form (host side)
+void pair_orbits(int nf, std::vector<int2>& orb) {
+  orb.clear();
+  for (int p = 0; p < nf; ++p)
+    for (int q = p + 1; q < nf; ++q) orb.push_back(make_int2(p, q));
+  for (int p = 0; p < nf; ++p) orb.push_back(make_int2(p, p));
 }
 
-// Lower-triangle tiles in launch order.  Every CTA streams the whole K extent of
-// its A' and B' rows, and about one CTA per SM is resident, so the order decides
-// what L2 can share: tiles go in bands of kGroupA A'-tiles, and within a band
-// column by column, so that the ~150 CTAs of a wave read about 12 A'-blocks and
-// 12 B'-blocks instead of ~150 different A'-blocks.
-void herk_tc_tiles(int64_t n2, std::vector<int2>& tiles) {
+size_t syrk_tc_split_bytes(int64_t n2, int64_t kcols) {
+  return (size_t)tc::NSLICE * n2 * tc::round_up(2 * kcols, tc::BK) * sizeof(__half) + 256;
+}
+
+// Lower-triangle tiles (ti >= tj) of the n2 x n2 E' in launch order, and their
+// index by (ti, tj).  Every CTA streams the whole K extent of its row blocks and
+// about one CTA per SM is resident, so the order decides what L2 can share:
+// tiles go in bands of kGroupA row blocks, and within a band column by column,
+// so that the ~150 CTAs of a wave read about 12 + 12 row blocks instead of ~150.
+void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_of) {
   constexpr int64_t kGroupA = 12;
   tiles.clear();
-  const int64_t mt = (2 * n2 + tc::BM - 1) / tc::BM, nt = (n2 + tc::BN - 1) / tc::BN;
-  for (int64_t t0 = 0; t0 < mt; t0 += kGroupA)
+  const int64_t nt = (n2 + tc::BM - 1) / tc::BM;
+  tile_of.assign(nt * nt, -1);
+  for (int64_t t0 = 0; t0 < nt; t0 += kGroupA)
     for (int64_t tj = 0; tj < nt; ++tj)
-      for (int64_t ti = t0; ti < std::min(mt, t0 + kGroupA); ++ti)
-        if (ti * (tc::BM / 2) + (tc::BM / 2 - 1) >= tj * tc::BN) tiles.push_back(make_int2((int)ti, (int)tj));
+      for (int64_t ti = t0; ti < std::min(nt, t0 + kGroupA); ++ti)
+        if (ti >= tj) {
+          tile_of[ti * nt + tj] = (int)tiles.size();
+          tiles.push_back(make_int2((int)ti, (int)tj));
+        }
 }
 
-size_t herk_tc_ws_bytes(int64_t ntiles) { return (size_t)ntiles * tc::BN * tc::BM * 2 * sizeof(float); }
+size_t syrk_tc_ws_bytes(int64_t ntiles) { return (size_t)ntiles * tc::BN * tc::BM * 2 * sizeof(float); }
 
-// Row exponents over the whole row: element (a, k) = B[slot(Q) sQ + a sA + J], k = Q nJ + J < K.
-cudaError_t herk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                             int64_t n2, int64_t K, int* row_exp) {
+cudaError_t syrk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                             int nS, const int2* orb, int nf, int* row_exp) {
   tc::BView bv{B, sQ, sA, nJ, qmap};
-  tc::row_scale_kernel<<<(unsigned)n2, 256, 0, st>>>(bv, n2, K, row_exp);
+  const int no = nf * (nf + 1) / 2;
+  tc::rrow_scale_kernel<<<no, 256, 0, st>>>(bv, orb, nf, (int64_t)nS * nJ, row_exp);
   count_launch();
   return cudaGetLastError();
 }
 
-// ws (+)= slices of columns [k0, k0 + Kc) of B: one K chunk of E = B B^H.
-cudaError_t herk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                          int64_t n2, int64_t k0, int64_t Kc, const int* row_exp, void* split, const int2* tiles_d,
-                          int ntiles, void* ws, int accumulate, int* err) {
+cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                          const int2* orb, int nf, int j0, int nq, const int* row_exp, void* split,
+                          const int2* tiles_d, int ntiles, void* ws, int accumulate, int* err) {
   using namespace tc;
-  if (n2 <= 0 || Kc <= 0 || ntiles <= 0) return cudaSuccess;
-  const int64_t K2 = ((2 * Kc + BK - 1) / BK) * BK;
+  const int64_t n2 = (int64_t)nf * nf;
+  if (n2 <= 0 || nq <= 0 || ntiles <= 0) return cudaSuccess;
+  const int64_t K2 = round_up(2 * (int64_t)nq * nJ, BK);
   __half* S1 = reinterpret_cast<__half*>(split);
-  __half* S2 = S1 + (size_t)(2 * n2) * K2;
-  __half* S3 = S2 + (size_t)(2 * n2) * K2;
+  __half* S2 = S1 + (size_t)n2 * K2;
+  __half* S3 = S2 + (size_t)n2 * K2;
   BView bv{B, sQ, sA, nJ, qmap};
-  split_kernel<<<nblk(n2 * (K2 / 2)), 256, 0, st>>>(bv, n2, k0, Kc, K2, row_exp, S1, S2, S3);
+  const int no = nf * (nf + 1) / 2;
+  rsplit_kernel<<<nblk((int64_t)no * (K2 / 2)), 256, 0, st>>>(bv, orb, nf, j0, nq, K2, row_exp, S1, S2, S3);
   count_launch();
-  CUtensorMap mA[3], mB[3];
+  CUtensorMap m[3];
   __half* sl[3] = {S1, S2, S3};
   for (int i = 0; i < 3; ++i)
-    if (!make_map(&mA[i], sl[i], K2, 2 * n2, K2, BM) || !make_map(&mB[i], sl[i], K2, n2, 2 * K2, BN))
-      return cudaErrorInvalidValue;
+    if (!make_map(&m[i], sl[i], K2, n2, K2, BM)) return cudaErrorInvalidValue;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-  cudaError_t e = cudaFuncSetAttribute(herk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   float* wh = reinterpret_cast<float*>(ws);
   float* wl = wh + (size_t)ntiles * BN * BM;
   TileArgs args{tiles_d, wh, wl, (int)(K2 / BK), accumulate, err};
-  herk_tc_kernel<<<ntiles, NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], args);
+  syrk_tc_kernel<<<ntiles, NTHREADS, smem, st>>>(m[0], m[1], m[2], m[0], m[1], m[2], args);
   count_launch();
   return cudaGetLastError();
 }
 
-// E (complex128 n2 x n2, full Hermitian) = scale * 2^-(e_a + e_b) * workspace.
-cudaError_t herk_tc_finish(cudaStream_t st, const void* ws, const int2* tiles_d, int ntiles, int64_t n2,
+cudaError_t syrk_tc_finish(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb, int nf,
                            const int* row_exp, double scale, double2* E) {
   using namespace tc;
   const float* wh = reinterpret_cast<const float*>(ws);
   const float* wl = wh + (size_t)ntiles * BN * BM;
-  herk_finish_kernel<<<nblk((int64_t)ntiles * BN * (BM / 2)), 256, 0, st>>>(wh, wl, tiles_d, ntiles, n2, row_exp,
-                                                                            scale, E);
+  const int64_t n2 = (int64_t)nf * nf, nt = (n2 + BM - 1) / BM, no = (int64_t)nf * (nf + 1) / 2;
+  syrk_finish_kernel<<<nblk(no * no), 256, 0, st>>>(wh, wl, tile_of_d, (int)nt, orb, nf, row_exp, scale, E);
   count_launch();
   return cudaGetLastError();
-}
-
-// One-shot E = scale * B B^H for B complex64 n2 x K with row pitch ldb.
-cudaError_t herk_tc(cudaStream_t st, const float2* B, int64_t n2, int64_t K, int64_t ldb, double scale,
-                    void* split, const int2* tiles_d, int ntiles, void* ws, int* row_exp, int* err, double2* E) {
-  cudaError_t e = herk_tc_rowscale(st, B, 0, ldb, K, nullptr, n2, K, row_exp);
-  if (e != cudaSuccess) return e;
-  e = herk_tc_chunk(st, B, 0, ldb, K, nullptr, n2, 0, K, row_exp, split, tiles_d, ntiles, ws, 0, err);
-  if (e != cudaSuccess) return e;
-  return herk_tc_finish(st, ws, tiles_d, ntiles, n2, row_exp, scale, E);
 }
 
 // ---- B = M L on the tensor cores, four slices (host side)
-int mlgemm_tc_kp(int np) { return ((2 * np + tc::BK - 1) / tc::BK) * tc::BK; }
-int mlgemm_tc_np_pad(int np) { return ((np + tc::MBN - 1) / tc::MBN) * tc::MBN; }
-bool mlgemm_tc_supported(int np) { return np > 0 && mlgemm_tc_kp(np) <= tc::kMlMaxK; }
-size_t mlgemm_tc_lslice_bytes(int nk, int np) {
-  return (size_t)tc::MSL * nk * mlgemm_tc_np_pad(np) * mlgemm_tc_kp(np) * sizeof(__half) + 256;
+int mlgemm_tc_kp(int rp) { return (int)tc::round_up(2 * (int64_t)rp, tc::BK); }
+int mlgemm_tc_nj_pad(int nj) { return (int)tc::round_up(nj, tc::MBN); }
+bool mlgemm_tc_supported(int rp) { return rp > 0 && mlgemm_tc_kp(rp) <= tc::kMlMaxK; }
+size_t mlgemm_tc_lslice_bytes(int nk, int rp, int nj) {
+  return (size_t)tc::MSL * nk * mlgemm_tc_nj_pad(nj) * mlgemm_tc_kp(rp) * sizeof(__half) + 256;
 }
-size_t mlgemm_tc_split_bytes(int64_t n2, int np, int nq) {
-  return (size_t)tc::MSL * nq * (2 * n2) * mlgemm_tc_kp(np) * sizeof(__half) + 256;
+size_t mlgemm_tc_split_bytes(int64_t n2, int rp, int nq) {
+  return (size_t)tc::MSL * nq * (2 * n2) * mlgemm_tc_kp(rp) * sizeof(__half) + 256;
 }
 
-cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, void* lsl,
-                              int* col_exp) {
+cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, const int* perm,
+                              const int* rank, int rp, int nj, void* lsl, int* col_exp) {
   using namespace tc;
-  const int Kp = mlgemm_tc_kp(np), npp = mlgemm_tc_np_pad(np);
-  const size_t per = (size_t)nk * npp * Kp;
+  const int Kp = mlgemm_tc_kp(rp), njp = mlgemm_tc_nj_pad(nj);
+  const size_t per = (size_t)nk * njp * Kp;
   __half* S1 = reinterpret_cast<__half*>(lsl);
-  lslice_kernel<<<dim3(npp, nk), 128, 0, st>>>(L, sw, np, npp, Kp, S1, S1 + per, S1 + 2 * per, S1 + 3 * per,
-                                                col_exp);
+  lslice_kernel<<<dim3(njp, nk), 128, 0, st>>>(L, sw, np, perm, rank, nj, njp, Kp, S1, S1 + per, S1 + 2 * per,
+                                                S1 + 3 * per, col_exp);
   count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* qmap, int64_t n2, int np, int j0,
-                            int nq, const int* row_exp, void* split, const void* lsl, const int* col_exp, int nk,
-                            int* err) {
+cudaError_t mlgemm_tc_rowscale(cudaStream_t st, const float2* M, int64_t sq, int np, const int* qmap, int nS,
+                               const int* perm, const int* rank, int rp, int64_t n2, int* row_exp) {
+  tc::mrow_scale_kernel<<<(unsigned)n2, 256, 0, st>>>(M, sq, np, qmap, nS, perm, rank, rp, row_exp);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* qmap, int64_t n2, int np,
+                            const int* perm, const int* rank, int rp, int nj, int j0, int nq, const int* row_exp,
+                            void* split, const void* lsl, const int* col_exp, int nk, int* err) {
   using namespace tc;
   if (n2 <= 0 || nq <= 0) return cudaSuccess;
-  if (!mlgemm_tc_supported(np)) return cudaErrorInvalidValue;
-  const int Kp = mlgemm_tc_kp(np), npp = mlgemm_tc_np_pad(np);
-  const size_t pa = (size_t)nq * (2 * n2) * Kp, pb = (size_t)nk * npp * Kp;
+  if (!mlgemm_tc_supported(rp)) return cudaErrorInvalidValue;
+  const int Kp = mlgemm_tc_kp(rp), njp = mlgemm_tc_nj_pad(nj);
+  const size_t pa = (size_t)nq * (2 * n2) * Kp, pb = (size_t)nk * njp * Kp;
   __half* S1 = reinterpret_cast<__half*>(split);
-  BView mv{M, sq, np, np, qmap};
-  msplit_kernel<<<nblk((int64_t)nq * n2 * (Kp / 2)), 256, 0, st>>>(mv, n2, np, j0, nq, Kp, row_exp, S1, S1 + pa,
-                                                                   S1 + 2 * pa, S1 + 3 * pa);
+  msplit_kernel<<<nblk((int64_t)nq * n2 * (Kp / 2)), 256, 0, st>>>(M, sq, np, qmap, perm, rank, n2, j0, nq, Kp,
+                                                                   row_exp, S1, S1 + pa, S1 + 2 * pa, S1 + 3 * pa);
   count_launch();
   const __half* L1 = reinterpret_cast<const __half*>(lsl);
   CUtensorMap mA[MSL], mB[MSL];
   for (int i = 0; i < MSL; ++i)
     if (!make_map(&mA[i], S1 + i * pa, Kp, (int64_t)nq * 2 * n2, Kp, BM) ||
-        !make_map(&mB[i], L1 + i * pb, Kp, (int64_t)nk * npp, Kp, MBN))
+        !make_map(&mB[i], L1 + i * pb, Kp, (int64_t)nk * njp, Kp, MBN))
       return cudaErrorInvalidValue;
   const size_t smem = (size_t)STAGES * MSTAGE_BYTES + 1024 + 256;
   cudaError_t e = cudaFuncSetAttribute(mlgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int mt = (int)((2 * n2 + BM - 1) / BM), ntj = npp / MBN;
-  MlArgs args{M, qmap, row_exp, col_exp, sq, (int)n2, np, npp, j0, Kp / BK, err};
+  const int mt = (int)((2 * n2 + BM - 1) / BM), ntj = njp / MBN;
+  MlArgs args{M, qmap, row_exp, col_exp, sq, (int)n2, nj, njp, j0, Kp / BK, err};
   mlgemm_tc_kernel<<<dim3(mt * ntj, nq), NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mA[3], mB[0], mB[1], mB[2],
                                                                 mB[3], args);
   count_launch();

@@ -39,6 +39,7 @@ TAG_SIZES = 4
 TAG_REAL = 5
 TAG_SINGLEK = 6
 TAG_EPS = 7
+TAG_POINTS = 8
 
 SEED_BASE = 20260000
 
@@ -172,6 +173,15 @@ def orbital_energies(cell: Cell, seed: int, n_occ: int) -> np.ndarray:
     occ = np.sort(rng.uniform(-1.0, -0.2, size=(nk, n_occ)), axis=1)
     vir = np.sort(rng.uniform(0.2, 2.0, size=(nk, nao - n_occ)), axis=1)
     return np.concatenate([occ, vir], axis=1)
+
+
+def seeded_points(cell: Cell, n_p: int, seed: int) -> np.ndarray:
+    """n_p distinct grid indices drawn uniformly (a seeded stand-in for the
+    interpolation points, given to both sides when the selection itself is
+    not what a test compares)."""
+    if n_p > cell.ngrid:
+        raise ValueError("more points than grid points")
+    return np.sort(_rng(seed, TAG_POINTS).choice(cell.ngrid, size=n_p, replace=False)).astype(np.int32)
 
 
 def make_fragment(cell: Cell, seed: int, index: int, norb: int,

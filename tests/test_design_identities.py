@@ -1,0 +1,124 @@
+"""Identities the GPU path is built on, checked in FP64 on the oracle's arrays.
+
+The fragment contraction on the GPU does not form E = sum_q M^q V^q M^q^H as
+written (Eq. 19).  It relies on two exact rewritings, which these CPU tests
+check on the oracle's pair tensor and Coulomb metric:
+
+* the structural zeros of L^q (V^q = L^q L^q^H with L^q = W^T L_xi): L^q is
+  nonzero only in the pivot rows of the truncated factor of Pi^q and in the
+  columns below the rank of V_xi, so B^q = M^q L^q needs only those;
+* the real symmetric form: in the basis u = e_(pq) + e_(qp), v = i (e_(pq) - e_(qp)),
+  e_(pp) fixed by the time-reversal symmetry E_{s(a)s(b)} = conj(E_ab), E is real,
+  and equals c sum_{q in S} [Re R^q, Im R^q][Re R^q, Im R^q]^T over the half set S.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_16379_gb300 import workloads as W
+
+
+def _cell(kmesh):
+    shells = [W.Shell(0, 0, (0.6,), (1.0,)), W.Shell(1, 0, (0.9,), (1.0,)), W.Shell(0, 1, (1.2,), (1.0,))]
+    return W.custom_cell(5.0, [[0, 0, 0], [0.37, 0.52, 0.21]], shells, kmesh, 10)
+
+
+def _half_set(kmesh):
+    """The q of the paired sum and their weights: m0 in [0, n0/2], and m1 in
+    [0, n1/2] when m0 is its own negative; weight 1/2 when m0 and m1 both are."""
+    n0, n1, n2 = kmesh
+    out = []
+    for q in range(n0 * n1 * n2):
+        m0, m1 = q // (n1 * n2), (q // n2) % n1
+        self0 = m0 == 0 or 2 * m0 == n0
+        self1 = m1 == 0 or 2 * m1 == n1
+        if 2 * m0 <= n0 and (not self0 or 2 * m1 <= n1):
+            out.append((q, 0.5 if (self0 and self1) else 1.0))
+    return out
+
+
+def _rows(nf):
+    """Row transform to the time-reversal basis (unnormalised) and its inverse map."""
+    n2 = nf * nf
+    pairs = [(p, q) for p in range(nf) for q in range(p + 1, nf)]
+    P = len(pairs)
+    T = np.zeros((n2, n2), np.complex128)
+    Cm = np.zeros((n2, n2), np.complex128)
+    for o, (p, q) in enumerate(pairs):
+        a, s = p * nf + q, q * nf + p
+        T[2 * o, a], T[2 * o, s] = 1.0, 1.0            # u = B_(pq) + B_(qp)
+        T[2 * o + 1, a], T[2 * o + 1, s] = -1j, 1j      # v = -i (B_(pq) - B_(qp))
+        Cm[a, 2 * o], Cm[a, 2 * o + 1] = 0.5, 0.5j
+        Cm[s, 2 * o], Cm[s, 2 * o + 1] = 0.5, -0.5j
+    for p in range(nf):
+        T[2 * P + p, p * nf + p] = 1.0
+        Cm[p * nf + p, 2 * P + p] = 1.0
+    return T, Cm
+
+
+@pytest.mark.parametrize("kmesh", [(3, 3, 3), (4, 2, 3)])
+def test_real_symmetric_form_of_E(kmesh):
+    cell = _cell(kmesh)
+    r = O.run_isdf(cell, 12, 7, solve_tol=1e-14)
+    nk, nf = cell.nkpts, 4
+    frag = W.make_fragment(cell, 11, 2, nf)
+    M = O.pair_tensor(O.fragment_T(r["X"], frag.C), cell.kmesh)
+    V = r["V"]
+    E = O.fragment_E(M, V, nk)
+    T, Cm = _rows(nf)
+    # any factor of each V^q will do: the identity is one of M V M^H
+    Ep = np.zeros((nf * nf, nf * nf))
+    for q, w in _half_set(kmesh):
+        lam, U = np.linalg.eigh(V[q])
+        L = U * np.sqrt(np.clip(lam, 0.0, None))[None, :]
+        R = T @ (M[q] @ L)
+        Rr = np.hstack([R.real, R.imag])
+        Ep += w * Rr @ Rr.T
+    Ep *= 2.0 / nk
+    scale = np.abs(E).max()
+    # E in the time-reversal basis is real and equals the real half-set product
+    Et = T @ E @ T.conj().T
+    assert np.abs(Et.imag).max() < 1e-10 * scale
+    assert np.abs(Et.real - Ep).max() < 1e-10 * scale
+    # the finish map E = Cm E' Cm^H recovers E
+    assert np.abs(Cm @ Ep @ Cm.conj().T - E).max() < 1e-10 * scale
+
+
+def test_structural_zeros_of_the_coulomb_factor():
+    """L^q = W^T L_xi with W = L_S^{-1} scattered to the pivot columns: its rows
+    outside the pivots of Pi^q and its columns beyond the rank of V_xi vanish, and
+    M L over the gathered pivot columns equals the full product."""
+    cell = _cell((3, 3, 3))
+    r = O.run_isdf(cell, 20, 7, solve_tol=1e-6)
+    nk = cell.nkpts
+    frag = W.make_fragment(cell, 11, 2, 3)
+    M = O.pair_tensor(O.fragment_T(r["X"], frag.C), cell.kmesh)
+    seen_truncated = False
+    for q in range(nk):
+        L, perm, rank = O.pchol(r["Pi"][q], 1e-6)
+        n = r["Pi"].shape[1]
+        seen_truncated |= rank < n
+        Wm = np.zeros((n, n), np.complex128)
+        LS = L[perm[:rank], :rank]
+        Wm[:rank, perm[:rank]] = np.linalg.inv(LS)
+        # xi = W eta has zero rows beyond the rank; zeta = W^H xi is the basic solution of the fit
+        xi = Wm @ r["eta"][q]
+        assert np.abs(xi[rank:]).max() == 0.0
+        zeta = Wm.conj().T @ xi
+        assert np.abs(zeta - r["zeta"][q]).max() < 1e-8 * np.abs(r["zeta"][q]).max()
+        # V_xi = L_xi L_xi^H has rank <= r_q, so L^q = W^T L_xi lives in the pivot rows
+        Vx = O.coulomb_metric(cell, xi[None], [q])[0]
+        lam, U = np.linalg.eigh(Vx)
+        keep = lam > 1e-12 * lam.max()
+        Lxi = U[:, keep] * np.sqrt(lam[keep])[None, :]
+        Lq = Wm.T @ Lxi
+        others = np.setdiff1d(np.arange(n), perm[:rank])
+        if others.size:
+            assert np.abs(Lq[others]).max() == 0.0
+        assert Lxi.shape[1] <= rank
+        full = M[q] @ Lq
+        gathered = M[q][:, perm[:rank]] @ Lq[perm[:rank]]
+        assert np.abs(full - gathered).max() <= 1e-13 * np.abs(full).max()
+        # and it reproduces V^q
+        assert np.abs(Lq @ Lq.conj().T - r["V"][q]).max() < 1e-8 * np.abs(r["V"][q]).max()
+    assert seen_truncated

@@ -1,0 +1,156 @@
+"""GPU path against the FP64 oracle at the large configurations, on samples.
+
+The oracle's direct k-sums are too slow for whole c3-c5 builds, so these tests
+compare what it can compute one unit at a time:
+
+* c3 as configured (Nk = 64, 32^3 grid, N_P = 500, 52 AOs): Pi^q for sampled q
+  and eta^q, zeta^q at sampled grid points (each grid point is an independent
+  column of Eqs. 3 and 5).
+* the c4 and c5 k-meshes (Nk = 216 and 1000, N_P = 300, 26 AOs) on an 8^3 grid,
+  where the grid-sized arrays are small: V^q for sampled q (Eq. 6), and at
+  Nk = 216 the fragment ERIs of a fragment and of a 6-orbital block of a
+  120-orbital fragment over every q (Eqs. 19-20), in both precisions.
+
+Both sides take the same seeded interpolation points (isdf_set_points); the
+selection itself is compared bit for bit on the smaller cells elsewhere.
+Tolerances: 1e-8 Ha (FP64 path) and 1e-6 Ha (mixed path) for ERIs and traces;
+the fit quantities are FP64 in both paths.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_16379_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TAU = 1e-7
+FP64_TOL = 1e-8
+MIXED_TOL = 1e-6
+
+
+def _setup(torch, wl, prec, ips):
+    from paper_2601_16379_gb300 import binding as B
+    g = B.Isdf(wl.cell, prec)
+    g.set_points(ips)
+    g.fit_zeta(TAU)
+    return g
+
+
+def _get_cols(torch, g, what, shape, qs, cols):
+    """isdf_get of a [Nk][N_P][N_g] array, reduced on the device to the sampled q and columns."""
+    full = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    g.get(what, full)
+    out = full[list(qs)][:, :, list(cols)].cpu().numpy()
+    del full
+    torch.cuda.empty_cache()
+    return out
+
+
+def _oracle_fit_samples(cell, ips, qs, cols):
+    """Oracle Pi^q, eta^q and zeta^q (at the sampled grid columns) for the sampled q."""
+    pts = O.grid_points(cell)
+    need = np.union1d(ips, cols)
+    phi = O.bloch_ao(cell, pts=pts[need])               # Phi^k at the points needed only
+    X = O.interp_vectors(phi, np.searchsorted(need, ips))
+    Pi = O.metric_pi(X, cell.kmesh, qs=qs)
+    eta = O.rhs_eta(X, phi[:, :, np.searchsorted(need, cols)], cell.kmesh, qs=qs)
+    zeta, _ = O.fit_zeta(Pi, eta, TAU)
+    return X, Pi, eta, zeta
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_c3_fit_sampled(cuda, lib_built):
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl = W.workload("c3", with_fragments=False)
+    cell = wl.cell
+    ips = W.seeded_points(cell, wl.n_p, wl.seed)
+    rng = np.random.default_rng(3)
+    qs = [0, 5, 42]
+    cols = np.sort(rng.choice(cell.ngrid, size=48, replace=False))
+    X, Pi, eta, zeta = _oracle_fit_samples(cell, ips, qs, cols)
+    g = _setup(torch, wl, B.ISDF_FP64, ips)
+    nk, npp, ng = cell.nkpts, wl.n_p, cell.ngrid
+    Xg = torch.empty((nk, npp, cell.nao), dtype=torch.complex128, device="cuda")
+    g.get(0, Xg)
+    assert _rel(Xg.cpu().numpy(), X) < 1e-13
+    Pig = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
+    g.get(1, Pig)
+    assert _rel(Pig.cpu().numpy()[qs], Pi) < 1e-12
+    assert _rel(_get_cols(torch, g, 2, (nk, npp, ng), qs, cols), eta) < 1e-12
+    assert _rel(_get_cols(torch, g, 3, (nk, npp, ng), qs, cols), zeta) < 1e-7
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def c4_small():
+    """c4 k-mesh (6^3, N_P = 300, 26 AOs) on an 8^3 grid: the oracle's full fit and V^q."""
+    wl = W.workload("c4", mesh=8, with_fragments=False)
+    ips = W.seeded_points(wl.cell, wl.n_p, wl.seed)
+    r = O.run_isdf(wl.cell, wl.n_p, wl.seed, solve_tol=TAU, ips=ips)
+    return wl, ips, r
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_c4_kmesh_metric_and_eris(cuda, lib_built, c4_small, prec):
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, ips, r = c4_small
+    cell = wl.cell
+    nk, npp = cell.nkpts, wl.n_p
+    g = _setup(torch, wl, prec, ips)
+    V = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
+    g.coulomb_metric(V)
+    if prec == B.ISDF_FP64:
+        # (the mixed path's V^q carries its complex64 Coulomb GEMM times the ill-conditioned
+        # W; what it must get right is E, checked below)
+        assert _rel(V.cpu().numpy(), r["V"]) < 1e-8
+    tol = FP64_TOL if prec == B.ISDF_FP64 else MIXED_TOL
+    dt = torch.complex128 if prec == B.ISDF_FP64 else torch.complex64
+    small = W.make_fragment(cell, wl.seed, 0, 12)
+    big = W.make_fragment(cell, wl.seed, 1, 120)
+    Cs = [torch.from_numpy(f.C).cuda() for f in (small, big)]
+    gs = [torch.from_numpy(f.gamma).cuda() for f in (small, big)]
+    outs = [torch.empty((f.norb,) * 4, dtype=dt, device="cuda") for f in (small, big)]
+    ej, ek = g.fragment_eri(Cs, gs, outs)
+    torch.cuda.synchronize()
+    # whole 12-orbital fragment: ERIs and traces
+    ref = O.fragment_eri(r["X"], r["V"], small.C, cell.kmesh)
+    rj, rk = O.traces(ref, small.gamma)
+    assert np.abs(outs[0].cpu().numpy().astype(np.complex128) - ref).max() < tol
+    assert abs(ej[0] - rj) < tol and abs(ek[0] - rk) < tol
+    # a 6-orbital block of the 120-orbital fragment: its ERIs are those of the sub-fragment
+    sub = np.array([0, 17, 42, 63, 101, 119])
+    refb = O.fragment_eri(r["X"], r["V"], big.C[:, :, sub], cell.kmesh)
+    blk = outs[1][sub][:, sub][:, :, sub][:, :, :, sub].cpu().numpy().astype(np.complex128)
+    assert np.abs(blk - refb).max() < tol
+    g.close()
+
+
+def test_c5_kmesh_fit_and_metric_sampled(cuda, lib_built):
+    """Nk = 1000 (c5's mesh) on an 8^3 grid: Pi^q, eta^q, zeta^q and V^q for sampled q."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl = W.workload("c5", mesh=8, with_fragments=False)
+    cell = wl.cell
+    nk, npp, ng = cell.nkpts, wl.n_p, cell.ngrid
+    ips = W.seeded_points(cell, wl.n_p, wl.seed)
+    qs = [0, 111, 555, 999]
+    cols = np.arange(ng)
+    X, Pi, eta, zeta = _oracle_fit_samples(cell, ips, qs, cols)
+    Vref = O.coulomb_metric(cell, zeta, qs)
+    g = _setup(torch, wl, B.ISDF_FP64, ips)
+    Pig = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
+    g.get(1, Pig)
+    assert _rel(Pig.cpu().numpy()[qs], Pi) < 1e-12
+    del Pig
+    assert _rel(_get_cols(torch, g, 2, (nk, npp, ng), qs, cols), eta) < 1e-12
+    assert _rel(_get_cols(torch, g, 3, (nk, npp, ng), qs, cols), zeta) < 1e-7
+    V = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
+    g.coulomb_metric(V)
+    assert _rel(V.cpu().numpy()[qs], Vref) < 1e-8
+    g.close()
