@@ -193,6 +193,7 @@ def run_gpu(args, rank, world, local_rank):
     else:
         shared = torch.empty(max(f.norb for f in frags) ** 4, dtype=dt_out, device="cuda")
         outs = [shared[: f.norb ** 4].view((f.norb,) * 4) for f in frags]
+        del shared   # kept alive by the views
         out_mode = f"one reused buffer (all {len(frags)} ERI tensors: {out_bytes / 2**30:.0f} GiB)"
 
     ranks_q = {}
@@ -332,18 +333,30 @@ def run_gpu(args, rank, world, local_rank):
         "stages_ms_per_step": {k: v[0] / done for k, v in stage.items()},
         "clocks": clk,
         "traces_fragment0": {"E_J": float(ej[0]), "E_K": float(ek[0])},
+        "autotune": g.autotune_report() if prec == B.ISDF_MIXED else None,
     }
     fit_s = sum(stage[k][0] for k in ("points", "fit", "coulomb")) / done / 1e3
-    if rank == 0 and prec == B.ISDF_MIXED and not args.no_accuracy:
-        # outside the timed region: free this handle's HBM, then compare against the FP64 path
-        est = accuracy_cost_s(wl, fit_s)
-        if budget.left() > est + CPU_BASELINE_S:
-            del outs
+    held = {"outs": outs}
+    del outs
+
+    def release():
+        # outside the timed region: free this handle's HBM before other handles run
+        if held:
+            held.clear()
             g.close()
             torch.cuda.empty_cache()
+
+    if rank == 0 and prec == B.ISDF_MIXED and not args.no_accuracy:
+        est = accuracy_cost_s(wl, fit_s)
+        if budget.left() > est + CPU_BASELINE_S:
+            release()
             result["accuracy"] = accuracy_vs_fp64(wl, args.solve_tol)
         else:
             result["accuracy"] = {"skipped": f"wall-clock budget ({budget.left():.0f} s left, ~{est:.0f} s needed)"}
+    if rank == 0 and args.nk_scan and args.workload == "c5" and not (args.kmesh or args.mesh or args.frag_sizes):
+        # linear cost in Nk (Section IV): the same fragment set on smaller k-meshes
+        release()
+        result["nk_scan"] = nk_scan(args, prec, budget)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget, kmesh=args.kmesh,
                                               mesh=args.mesh, frag_sizes=_frag_sizes(args))
@@ -352,6 +365,49 @@ def run_gpu(args, rank, world, local_rank):
         print(json.dumps(result))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def nk_scan(args, prec, budget, meshes=(2, 4, 6, 8)):
+    """Build time of the workload's fragment set on smaller k-meshes (one warm-up
+    and one timed step each, CUDA events), while the budget keeps CPU_BASELINE_S."""
+    import torch
+    from paper_2601_16379_gb300 import binding as B
+    from paper_2601_16379_gb300 import workloads as W
+
+    pts = []
+    for n in meshes:
+        if budget.left() < CPU_BASELINE_S + 30.0 * (n / 4.0) ** 3 + 20.0:
+            pts.append({"nk": n ** 3, "skipped": "wall-clock budget"})
+            continue
+        wl = W.workload(args.workload, kmesh=n)
+        g = B.Isdf(wl.cell, prec)
+        dt = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
+        Cs = [torch.from_numpy(f.C).cuda() for f in wl.fragments]
+        gs = [torch.from_numpy(f.gamma).cuda() for f in wl.fragments]
+        nmax = max(f.norb for f in wl.fragments)
+        shared = torch.empty(nmax ** 4, dtype=dt, device="cuda")
+        outs = [shared[: f.norb ** 4].view((f.norb,) * 4) for f in wl.fragments]
+
+        def step():
+            g.build_points(wl.n_p, wl.seed)
+            g.fit_zeta(args.solve_tol)
+            g.coulomb_metric()
+            g.fragment_eri(Cs, gs, outs)
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        pts.append({"nk": n ** 3, "s": round(t, 3), "s_per_k": round(t / n ** 3, 5)})
+        del outs, shared, Cs, gs
+        g.close()
+        torch.cuda.empty_cache()
+    return {"workload": "the same 64 fragments, cell and N_P on smaller k-meshes (1 warm-up + 1 timed step each)",
+            "points": pts}
 
 
 def _frag_sizes(args):
@@ -400,7 +456,10 @@ def accuracy_cost_s(wl, fit_s):
 def accuracy_vs_fp64(wl, solve_tol):
     """Max-abs ERI error and |dE_J|, |dE_K| (Ha) of the mixed path against the
     FP64 path on the same GPU, for the smallest fragment and the largest one
-    whose FP64 contraction fits FP64_FLOP_BUDGET."""
+    whose FP64 contraction fits FP64_FLOP_BUDGET.  The FP64 path is timed on
+    the way (CUDA events): points + fit + Coulomb metric, and each sampled
+    fragment on its own, from which its whole build is extrapolated with
+    t(n_f) = a n_f^4 + b n_f^2 (the E and pair/B terms) fitted to the two."""
     import torch
     from paper_2601_16379_gb300 import binding as B
 
@@ -408,20 +467,39 @@ def accuracy_vs_fp64(wl, solve_tol):
     nsum = _paired_q_count(cell.kmesh)
     sizes = [f.norb for f in wl.fragments]
     ok = [i for i, s in enumerate(sizes) if 4.0 * (s * s) ** 2 * nsum * np_ <= FP64_FLOP_BUDGET]
-    pick = sorted({int(np.argmin(sizes))} | ({max(ok, key=lambda i: sizes[i])} if ok else set()))
+    # largest first, so that the smaller one reuses its workspaces (no allocation in its timing)
+    pick = sorted({int(np.argmin(sizes))} | ({max(ok, key=lambda i: sizes[i])} if ok else set()),
+                  key=lambda i: -sizes[i])
     frags = [wl.fragments[i] for i in pick]
-    res = {}
+    res, timing = {}, {}
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
     for prec in (B.ISDF_FP64, B.ISDF_MIXED):
         g = B.Isdf(cell, prec)
+        torch.cuda.synchronize()
+        e0 = ev()
         g.build_points(np_, wl.seed)
         g.fit_zeta(solve_tol)
         g.coulomb_metric()
+        e1 = ev()
         dt = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
         Cs = [torch.from_numpy(f.C).cuda() for f in frags]
         gs = [torch.from_numpy(f.gamma).cuda() for f in frags]
         outs = [torch.empty((f.norb,) * 4, dtype=dt, device="cuda") for f in frags]
-        ej, ek = g.fragment_eri(Cs, gs, outs)
-        torch.cuda.synchronize()
+        ej, ek, t_frag = [], [], []
+        for i in range(len(frags)):
+            a = ev()
+            x, y = g.fragment_eri([Cs[i]], [gs[i]], [outs[i]])
+            b = ev()
+            torch.cuda.synchronize()
+            ej.append(x[0])
+            ek.append(y[0])
+            t_frag.append(a.elapsed_time(b) / 1e3)
+        timing[prec] = (e0.elapsed_time(e1) / 1e3, t_frag)
         res[prec] = ([o.cpu().numpy().astype(np.complex128) for o in outs], ej, ek)
         del outs, Cs, gs
         g.close()
@@ -431,11 +509,23 @@ def accuracy_vs_fp64(wl, solve_tol):
     for i, f in enumerate(frags):
         per.append({"n_f": f.norb, "max_abs_eri": float(np.abs(m[0][i] - d[0][i]).max()),
                     "dE_J": float(abs(m[1][i] - d[1][i])), "dE_K": float(abs(m[2][i] - d[2][i])),
-                    "E_J": float(d[1][i]), "E_K": float(d[2][i])})
+                    "E_J": float(d[1][i]), "E_K": float(d[2][i]),
+                    "fp64_s": round(timing[B.ISDF_FP64][1][i], 4), "mixed_s": round(timing[B.ISDF_MIXED][1][i], 4)})
     worst = max(max(x["max_abs_eri"], x["dE_J"], x["dE_K"]) for x in per)
-    return {"reference": "FP64 path on the same GPU (pinned to the FP64 oracle by the parity tests)",
-            "unit": "Ha", "tolerance": 1e-6, "max_error": worst, "within_tolerance": bool(worst <= 1e-6),
-            "fragments": per}
+    out = {"reference": "FP64 path on the same GPU (pinned to the FP64 oracle by the parity tests)",
+           "unit": "Ha", "tolerance": 1e-6, "max_error": worst, "within_tolerance": bool(worst <= 1e-6),
+           "fragments": per}
+    fit64, tf = timing[B.ISDF_FP64]
+    ns = [f.norb for f in frags]
+    if len(ns) == 2 and ns[0] != ns[1]:
+        A = np.array([[n ** 4, n ** 2] for n in ns], float)
+        a, b = np.linalg.solve(A, np.array(tf))
+        a, b = max(a, 0.0), max(b, 0.0)
+        total = fit64 + sum(a * n ** 4 + b * n ** 2 for n in sizes)
+        out["fp64_path"] = {"points_fit_coulomb_s": round(fit64, 3), "extrapolated_build_s": round(float(total), 1),
+                            "model": "fragment time a n_f^4 + b n_f^2 fitted to the two timed fragments, "
+                                     "summed over every fragment of the workload (extrapolated, not measured)"}
+    return out
 
 
 # ------------------------------------------------------- CPU oracle sample
@@ -566,10 +656,11 @@ def main():
     ap.add_argument("--budget-s", type=float, default=1200.0,
                     help="wall-clock seconds for the whole run (from process start); warm-ups and timed steps "
                          "beyond what fits are skipped and the executed counts reported")
-    ap.add_argument("--reserve-s", type=float, default=180.0,
+    ap.add_argument("--reserve-s", type=float, default=240.0,
                     help="seconds kept after the timed steps for the accuracy check and the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed vs FP64 comparison")
+    ap.add_argument("--nk-scan", type=int, default=1, help="1: time the c5 fragment set on 2^3..8^3 k-meshes too")
     ap.add_argument("--kmesh", type=int, default=None, help="k-mesh side override (Nk scan)")
     ap.add_argument("--mesh", type=int, default=None, help="real-space grid side override (small profiling cases)")
     ap.add_argument("--frag-sizes", type=str, default=None,

@@ -150,8 +150,10 @@ int isdf_coulomb_metric_eta(isdf_handle* h, void* V_out);
  *   ej_out[f]  E_J = 1/2 sum gamma_pq gamma_rs (pq|rs)          (host, may be NULL)
  *   ek_out[f]  E_K = -1/4 sum gamma_ps gamma_rq (pq|rs)         (host, may be NULL)
  * The traces are accumulated in FP64.  Fragments are done one after the
- * other on the handle's stream, so several entries of eri_out may name the
- * same buffer (each result then overwrites the previous one).
+ * other on the handle's stream (in MIXED mode small fragments are contracted
+ * in groups, each fragment's results still written in turn), so several
+ * entries of eri_out may name the same buffer (each result then overwrites the
+ * previous one).
  * Device memory: the handle keeps its scratch between calls; when an
  * allocation for a fragment fails, the grid-sized fit arrays (eta, xi) are
  * freed and the allocation retried (isdf_get of eta or zeta and
@@ -229,6 +231,25 @@ int isdf_set_time_reversal(isdf_handle* h, int enable);
  * 12 GiB; values below one q-point's slices give one q-point per chunk.
  * Returns ISDF_ERR_ARG for 0. */
 int isdf_set_workspace_limit(isdf_handle* h, uint64_t bytes);
+
+/* MIXED mode: schedule of the fragment contraction's tensor-core tiles.  The
+ * lower-triangle tiles of E' are launched in bands of row blocks (the CTAs of
+ * one wave then share their operand blocks in L2), by a kernel with one of two
+ * pipelines (0: K rows of 64 fp16 in 2 stages; 1: rows of 32 fp16 in 4 stages).
+ * With autotuning on (default), the first call that meets a tile list of a new
+ * size class times its first q-chunk with the schedules (pipeline, band) =
+ * (0, 12), (1, 12), (1, 6), (1, 24) and keeps the fastest for that class on this
+ * handle; off, (0, 12) or the schedule fixed below is used.  The schedule
+ * changes only the order of the
+ * work, not the results.  isdf_autotune_report writes the choices as a JSON list
+ * ([{"tiles": n, "pipeline": p, "band": b, "ms": [t0, t1, t2, t3]}, ...]) into
+ * buf (len bytes, NUL-terminated; ISDF_ERR_ARG if it does not fit). */
+int isdf_set_autotune(isdf_handle* h, int enable);
+int isdf_autotune_report(const isdf_handle* h, char* buf, size_t len);
+/* Fix the schedule instead of tuning it: pipeline 0 or 1 as above, band in
+ * [1, 64] row blocks per band (turns autotuning off; isdf_set_autotune(h, 1)
+ * turns it back on).  ISDF_ERR_ARG for other values. */
+int isdf_set_tile_schedule(isdf_handle* h, int pipeline, int band);
 
 /* Inspection of intermediate results (device outputs, complex128):
  *   what = 0  X   [Nk][N_P][N_AO]

@@ -26,7 +26,9 @@ STATUS = {0: "ISDF_OK", -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_OOM", -3: "ISDF_ERR_CU
 EXPORTS = ["isdf_create", "isdf_build_points", "isdf_set_points", "isdf_fit_zeta",
            "isdf_coulomb_metric", "isdf_coulomb_metric_eta", "isdf_fragment_eri", "isdf_exchange",
            "isdf_ao_eri", "isdf_sos_polarizability",
-           "isdf_set_time_reversal", "isdf_set_workspace_limit", "isdf_get", "isdf_sizes",
+           "isdf_set_time_reversal", "isdf_set_workspace_limit", "isdf_set_autotune", "isdf_autotune_report",
+           "isdf_set_tile_schedule",
+           "isdf_get", "isdf_sizes",
            "isdf_launch_count", "isdf_timing_enable", "isdf_timing_get", "isdf_eri_traces_noalloc",
            "isdf_last_error", "isdf_destroy"]
 
@@ -70,6 +72,9 @@ def load(path: Optional[str] = None) -> ct.CDLL:
     lib.isdf_sos_polarizability.argtypes = [vp, vp, ct.c_int, ct.c_int, dp, ct.c_double, vp, dp]
     lib.isdf_set_time_reversal.argtypes = [vp, ct.c_int]
     lib.isdf_set_workspace_limit.argtypes = [vp, ct.c_uint64]
+    lib.isdf_set_autotune.argtypes = [vp, ct.c_int]
+    lib.isdf_autotune_report.argtypes = [vp, ct.c_char_p, ct.c_size_t]
+    lib.isdf_set_tile_schedule.argtypes = [vp, ct.c_int, ct.c_int]
     lib.isdf_get.argtypes = [vp, ct.c_int, vp]
     lib.isdf_sizes.argtypes = [vp, ct.POINTER(ct.c_int64)]
     lib.isdf_launch_count.argtypes = [vp]
@@ -165,6 +170,21 @@ class Isdf:
     def set_workspace_limit(self, nbytes: int):
         """Device bytes for one q-chunk of the fp16 slices of the mixed contraction."""
         self._check(self.lib.isdf_set_workspace_limit(self.h, ct.c_uint64(int(nbytes))))
+
+    def set_autotune(self, enable: bool):
+        """Tile-order tuning of the mixed contraction (default on)."""
+        self._check(self.lib.isdf_set_autotune(self.h, 1 if enable else 0))
+
+    def set_tile_schedule(self, pipeline: int, band: int):
+        """Fix the tile schedule of the mixed contraction (turns tuning off)."""
+        self._check(self.lib.isdf_set_tile_schedule(self.h, int(pipeline), int(band)))
+
+    def autotune_report(self):
+        """The tile-order choices made so far, as a list of dicts."""
+        import json
+        buf = ct.create_string_buffer(1 << 16)
+        self._check(self.lib.isdf_autotune_report(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def stage_time(self, stage: int):
         """(device ms summed, launches, algorithmic flops summed) of a stage."""

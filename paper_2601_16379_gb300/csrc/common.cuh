@@ -135,41 +135,62 @@ cudaError_t grid_coulomb_fft_f(cudaStream_t st, float2* x, int rows_per_q, int q
                                const CellDev& c, const double2* dtw, void* work);
 void grid_twiddles(const int mesh[3], double2* host192);
 
+// Real k-mesh DFT out of place, keeping the q with qslot[q] >= 0 (complex64 output):
+//   out[qslot[q]][col] = scale sum_k e^{s 2 pi i m_q.m_k/n} in[k][col].
+cudaError_t kdft_real_f(cudaStream_t st, const float* in, float2* out, int64_t ncol, KMesh km, int s, float scale,
+                        const int* qslot);
+// Real pair rows of the time-reversal basis: for pairs o = (p < q) in lexicographic
+// order Zr[R][2o][I] = 2 Re(conj(t_p) t_q), Zr[R][2o+1][I] = 2 Im(conj(t_p) t_q), and
+// Zr[R][2P + p][I] = |t_p|^2 (P = n_f (n_f - 1)/2), t = t[R][I][p] complex64.
+// Rows row0 .. row0 + n_f^2 - 1 of a stack of `rows` rows: Zr[R][row0 + row][I].
+cudaError_t pair_products_real_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float* Zr, int64_t row0,
+                                 int64_t rows);
 // Fragment pair products Z[R][(p q)][I] = conj(t[R][I][p]) * t[R][I][q].
 cudaError_t pair_products(cudaStream_t st, const double2* t, int nk, int np, int nf, double2* Z);
-cudaError_t pair_products_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float2* Z);
 
 // eri[p][q][r][s] = E[(p q)][(s r)] * scale, and the traces.
 cudaError_t eri_permute(cudaStream_t st, const double2* E, int nf, double scale, double2* eri);
 cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale,
-                       const double2* gamma, double* out2);
+                       const double2* gamma, double* out4, double2* part);
 
 // Message of the last failed handle-free call on this thread.
 const char* noalloc_last_error();
 
 // Tensor-core E = sum_q B^q B^q^H (k_tc.cu) in the real symmetric form of the
-// time-reversal basis.  B is addressed as (a, k = Q nJ + J) -> B[slot(Q) sQ + a sA + J]
-// with slot(Q) = qmap[Q] (or Q when qmap is NULL), J < nJ, over the nS positions
-// of the sum.  orb: the swap orbits of pair_orbits (device copy, n_f (n_f+1)/2 entries).
-// Row exponents over all positions, then each chunk of positions (accumulate = 0
-// for the first), then the finish to E (complex128 n_f^2 x n_f^2, full) times scale.
+// time-reversal basis.  The rows of B are those of that basis (pair o = (p < q) ->
+// rows 2o, 2o + 1; diagonal p -> row 2P + p), addressed as
+// (a, k = Q nJ + J) -> B[slot(Q) sQ + a sA + J] with slot(Q) = qmap[Q] (or Q when
+// qmap is NULL), J < nJ, over the nS positions of the sum.  Row exponents over
+// all positions, then each chunk of positions (accumulate = 0 for the first),
+// then the finish to E (complex128 n_f^2 x n_f^2, full, in the pair basis (pq))
+// times scale; orb: the orbits of pair_orbits (device copy, n_f (n_f+1)/2 entries).
 void pair_orbits(int nf, std::vector<int2>& orb);
 size_t syrk_tc_split_bytes(int64_t n2, int64_t kcols);
-void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_of);
+void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_of, int band = 12);
 size_t syrk_tc_ws_bytes(int64_t ntiles);
 cudaError_t syrk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                             int nS, const int2* orb, int nf, int* row_exp);
+                             int nS, int64_t n2, int* row_exp);
+// cfg selects the pipeline of the tile kernel: 0 = K rows of 64 fp16 (128-byte
+// swizzle), 2 stages; 1 = rows of 32 fp16 (64-byte swizzle), 4 stages.
 cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                          const int2* orb, int nf, int j0, int nq, const int* row_exp, void* split,
-                          const int2* tiles_d, int ntiles, void* ws, int accumulate, int* err);
+                          int64_t n2, int j0, int nq, const int* row_exp, void* split, const int2* tiles_d, int ntiles,
+                          void* ws, int accumulate, int* err, int cfg = 0);
 cudaError_t syrk_tc_finish(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb, int nf,
                            const int* row_exp, double scale, double2* E);
+// The finish fused with the chemist's permutation (eri: complex64 [p][q][r][s], or
+// NULL) and the FP64 traces (gamma, or NULL: out4 = E_J, E_K, Im E_J, Im E_K);
+// part: syrk_tc_eri_part_count() double2 of scratch.  E is never stored.
+size_t syrk_tc_eri_part_count();
+cudaError_t syrk_tc_finish_eri(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb,
+                               int nf, const int* row_exp, double scale, float2* eri, const double2* gamma,
+                               double2* part, double* out4);
 // B^q = M^q L^q (w_q^{1/2} folded into L) on the tensor cores with four exact
 // integer slices, over the structural nonzeros of L^q only: the rp = max_q r_q
-// pivot columns perm_q[c] (c < rank_q) of M^q and the nj output columns; written
-// in place over M^q with row pitch nj.  prepare: slices of L for all q (once per
+// pivot columns perm_q[c] (c < rank_q) of M^q and the nj output columns.  M^q is
+// stored by position j in the sum (q = qmap[j]) with q stride sq; B^q is written
+// in place over it with row pitch nj.  prepare: slices of L for all q (once per
 // L); rowscale: exponents of the gathered M rows over the sum; chunk: the
-// positions j0..j0+nq-1 of the sum (q = qmap[j]).
+// positions j0..j0+nq-1 of the sum.
 int mlgemm_tc_kp(int rp);
 int mlgemm_tc_nj_pad(int nj);
 bool mlgemm_tc_supported(int rp);
@@ -192,11 +213,10 @@ cudaError_t scale_blocks(cudaStream_t st, const double2* L, int64_t per, int nb,
 cudaError_t scale_blocks_f(cudaStream_t st, const double2* L, int64_t per, int nb, const double* sw, float2* out);
 // out[I][mu n_ao + nu] = conj(x1[I][mu]) x2[I][nu] for I < np (x1, x2: [np][n_ao]).
 cudaError_t ao_pairs(cudaStream_t st, const double2* x1, const double2* x2, int np, int nao, double2* out);
-// k-SOS-MP2 pieces: weighted orbital columns, the k-convolution of the Green's
-// functions, and the per-Q partial traces of the opposite-spin energy.
+// k-SOS-MP2 pieces: weighted orbital columns and the per-Q partial traces of
+// the opposite-spin energy.
 cudaError_t scale_cols(cudaStream_t st, const double2* y, int nk, int np, int nmo, int c0, int nc, const double* eps,
                        double sgn_tau, double2* out);
-cudaError_t chi_kconv(cudaStream_t st, const double2* go, const double2* gv, const int kmesh[3], int np, double2* chi);
 cudaError_t sos_trace_parts(cudaStream_t st, const double2* t, const double2* chi, const int kmesh[3], int np,
                             double* part);
 // x[pairs[i].x] = conj(x[pairs[i].y]) for blocks of `per` elements (mirror_copy: plain copy).
@@ -204,6 +224,16 @@ cudaError_t mirror_conj(cudaStream_t st, double2* x, int64_t per, const int2* pa
 cudaError_t mirror_copy(cudaStream_t st, int32_t* x, int64_t per, const int2* pairs, int npairs);
 // out[b][I][J] = a[b][J][I] * c[b][I][J] for nb blocks of n x n.
 cudaError_t hadamard_t(cudaStream_t st, const double2* a, const double2* c, int n, int nb, double2* out);
+
+// FP64-accurate complex GEMM on the tensor cores for 2K <= 128 (k_emu.cu):
+// C_b = op(A_b) B_b, op 'N' or 'R' (conjugate), seven exact 7-bit slices per
+// operand.  work: zgemm_emu_work_bytes(M, N, K, batch) bytes; err: device word
+// set on a bounded-wait timeout.
+bool zgemm_emu_supported(int K);
+size_t zgemm_emu_work_bytes(int M, int N, int K, int batch);
+cudaError_t zgemm_emu(cudaStream_t st, char opA, int M, int N, int K, const double2* A, int64_t lda, int64_t sA,
+                      const double2* B, int64_t ldb, int64_t sB, double2* C, int64_t ldc, int64_t sC, int batch,
+                      void* work, int* err);
 
 // Precision conversions.
 cudaError_t z2c(cudaStream_t st, const double2* in, float2* out, int64_t n);

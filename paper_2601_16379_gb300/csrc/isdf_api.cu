@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -71,6 +72,18 @@ struct isdf_handle {
   size_t split_budget = (size_t)12 << 30;
   // pair q with -q in the fragment contraction (time-reversal symmetry)
   bool q_sym = true;
+  // schedule of the E' contraction's tiles, tuned per size class of the tile list
+  // unless fixed by isdf_set_tile_schedule
+  bool autotune = true;
+  int fixed_cfg = 0, fixed_band = 12;
+  struct TuneEntry {
+    int bucket;       // floor(log2(tiles))
+    int64_t ntiles;   // tile count it was tuned on
+    int cfg;          // chosen pipeline of the tile kernel
+    int band;         // chosen row blocks per band
+    float ms[4];      // first-chunk times of the candidate schedules
+  };
+  std::vector<TuneEntry> tune_log;
   // per-stage event timing
   static constexpr int kStages = 6;
   bool timing = false;
@@ -154,7 +167,7 @@ struct isdf_handle {
   // them, or isdf_coulomb_metric_eta, then needs a new isdf_fit_zeta).
   static bool in_frag_group(const std::string& n) { return n.rfind("frag_", 0) == 0 || n.rfind("tc_", 0) == 0; }
   static bool in_fit_group(const std::string& n) {
-    return n == "eta" || n == "xi" || n == "xi_f" || n == "grid_work";
+    return n == "eta" || n == "xi" || n == "xi_f" || n == "grid_work" || n == "grid_work_emu";
   }
   bool evict_other(const char* name) {
     const std::string n(name);
@@ -371,6 +384,93 @@ int finish_points(isdf_handle* h) {
 }
 
 }  // namespace
+
+// Groups of fragments for the mixed contraction.  A fragment whose lower
+// triangle of 128 x 128 tiles fills kWaves waves of the GPU or more goes alone;
+// smaller ones are stacked (ascending size) while the group's scratch -- pair
+// rows Z and M^q per row (padded to a tile boundary), and E per fragment -- stays
+// within what the largest fragment of the call needs alone (or kMinBytes).
+std::vector<std::vector<int>> fragment_groups(int n, const int32_t* n_orb, int nk, int nS, int np) {
+  constexpr int64_t kWaves = 4, kSMs = 152;
+  constexpr double kMinBytes = 4.0 * (1 << 30);
+  const double per_row = (double)np * (4.0 * nk + 8.0 * nS);
+  auto n2of = [&](int f) { return (int64_t)n_orb[f] * n_orb[f]; };
+  int64_t n2max = 0;
+  for (int f = 0; f < n; ++f) n2max = std::max(n2max, n2of(f));
+  const double cap = std::max(kMinBytes, per_row * (double)((n2max + 127) / 128 * 128) +
+                                             16.0 * (double)n2max * (double)n2max);
+  std::vector<int> order(n);
+  for (int f = 0; f < n; ++f) order[f] = f;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n2of(a) < n2of(b); });
+  std::vector<std::vector<int>> groups;
+  std::vector<int> cur;
+  double cur_bytes = 0.0;
+  for (int f : order) {
+    const int64_t n2 = n2of(f), nt = (n2 + 127) / 128;
+    if (nt * (nt + 1) / 2 >= kWaves * kSMs) {
+      groups.push_back({f});
+      continue;
+    }
+    const double b = per_row * (double)((n2 + 127) / 128 * 128) + 16.0 * (double)n2 * (double)n2;
+    if (!cur.empty() && cur_bytes + b > cap) {
+      groups.push_back(cur);
+      cur.clear();
+      cur_bytes = 0.0;
+    }
+    cur.push_back(f);
+    cur_bytes += b;
+  }
+  if (!cur.empty()) groups.push_back(cur);
+  // largest scratch first, so that the buffers are sized once per call
+  std::stable_sort(groups.begin(), groups.end(), [&](const std::vector<int>& a, const std::vector<int>& b) {
+    int64_t ra = 0, rb = 0;
+    for (int f : a) ra += (n2of(f) + 127) / 128 * 128;
+    for (int f : b) rb += (n2of(f) + 127) / 128 * 128;
+    return ra > rb;
+  });
+  return groups;
+}
+
+// Schedule of the E' contraction: the pipeline of the tile kernel (cfg 0: K rows of
+// 64 fp16 in 2 stages; cfg 1: rows of 32 fp16 in 4 stages) and the band width of
+// the tile order (row blocks per band, see syrk_tc_tiles).  Chosen per size class
+// of the tile list by timing the first q-chunk with each candidate on first use;
+// the choice is kept in the handle.  `trial(cfg, band)` runs that chunk (it
+// overwrites the workspace, so the caller's run of the chunk afterwards is
+// unaffected).
+struct TileSchedule {
+  int cfg, band;
+};
+constexpr TileSchedule kTileCandidates[4] = {{0, 12}, {1, 12}, {1, 6}, {1, 24}};
+
+TileSchedule tuned_schedule(isdf_handle* h, int64_t ntiles, const std::function<int(int, int)>& trial) {
+  const TileSchedule dflt = {h->fixed_cfg, h->fixed_band};
+  if (!h->autotune || ntiles < 2 * 152) return dflt;
+  const int bucket = (int)std::floor(std::log2((double)ntiles));
+  for (const auto& e : h->tune_log)
+    if (e.bucket == bucket) return {e.cfg, e.band};
+  isdf_handle::TuneEntry t{bucket, ntiles, dflt.cfg, dflt.band, {0, 0, 0, 0}};
+  float best = 1e30f;
+  for (int i = 0; i < 4; ++i) {
+    cudaEvent_t a = h->get_event(), b = h->get_event();
+    cudaEventRecord(a, h->st);
+    if (trial(kTileCandidates[i].cfg, kTileCandidates[i].band) != 0) return {-1, -1};
+    cudaEventRecord(b, h->st);
+    if (cudaEventSynchronize(b) != cudaSuccess) return {-1, -1};
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    h->event_pool.push_back(a);
+    h->event_pool.push_back(b);
+    t.ms[i] = ms;
+    if (ms < best) {
+      best = ms;
+      t.cfg = kTileCandidates[i].cfg;
+      t.band = kTileCandidates[i].band;
+    }
+  }
+  h->tune_log.push_back(t);
+  return {t.cfg, t.band};
+}
 
 // Shared tail of both Coulomb routes: factor V_xi = L_xi L_xi^H, L^q = W^T L_xi
 // (so V^q = L^q L^q^H), optional output of V^q, precision copies for the fragments.
@@ -608,10 +708,30 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
   CK(zgemm(h->st, 'R', 'T', np, np, nao, one, X, nao, (int64_t)np * nao, X, nao, (int64_t)np * nao, zero, Pi,
            np, (int64_t)np * np, nk));
   CK(kdft_cols(h->st, Pi, (int64_t)np * np, km, +1, -1, 1, 1.0 / nk));
-  // eta^q (Eq. 5): g^k_I(r) = sum_mu conj(X^k_I mu) Phi^k_mu(r), then the k-convolution
+  // eta^q (Eq. 5): g^k_I(r) = sum_mu conj(X^k_I mu) Phi^k_mu(r), then the k-convolution.
+  // In the mixed path g runs on the tensor cores with seven exact slices per
+  // operand (~2^-48 relative, FP64-class); the FP64 path keeps FP64 arithmetic.
   ENSURE(eta, double2, "eta", (size_t)nk * np * ng);
-  CK(zgemm(h->st, 'R', 'N', np, ng, nao, one, X, nao, (int64_t)np * nao, phi, ng, (int64_t)nao * ng, zero, eta,
-           ng, (int64_t)np * ng, nk));
+  if (h->prec == ISDF_MIXED && zgemm_emu_supported(nao)) {
+    const size_t per_k = zgemm_emu_work_bytes(np, ng, nao, 1);
+    const int nkc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nk, ((size_t)4 << 30) / per_k));
+    ENSURE(gw, uint8_t, "grid_work_emu", zgemm_emu_work_bytes(np, ng, nao, nkc));
+    ENSURE(tcw, int, "tc_words", 4);
+    CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
+    for (int k0 = 0; k0 < nk; k0 += nkc) {
+      const int nb = std::min(nkc, nk - k0);
+      CK(zgemm_emu(h->st, 'R', np, ng, nao, X + (int64_t)k0 * np * nao, nao, (int64_t)np * nao,
+                   phi + (int64_t)k0 * nao * ng, ng, (int64_t)nao * ng, eta + (int64_t)k0 * np * ng, ng,
+                   (int64_t)np * ng, nb, gw, tcw + 1));
+    }
+    int tc_err = 0;
+    CK(cudaMemcpyAsync(&tc_err, tcw + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (tc_err != 0) return fail(h, ISDF_ERR_TIMEOUT, "tensor-core GEMM of the fit: bounded wait expired (%d)", tc_err);
+  } else {
+    CK(zgemm(h->st, 'R', 'N', np, ng, nao, one, X, nao, (int64_t)np * nao, phi, ng, (int64_t)nao * ng, zero, eta,
+             ng, (int64_t)np * ng, nk));
+  }
   CK(kdft_cols(h->st, eta, (int64_t)np * ng, km, +1, -1, 1, 1.0 / nk));
   // Pi^q = L L^H (pivoted), W = L_S^{-1}
   ENSURE(LtPi, double2, "LtPi", (size_t)nk * np * np);
@@ -813,18 +933,28 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
   const int nj = (int)std::min<int64_t>(np, ((int64_t)nv + 3) / 4 * 4);  // columns of B^q
   const int32_t* permPi = (const int32_t*)h->buf("permPi");
   const int32_t* rankPi = (const int32_t*)h->buf("rankPi");
-  for (int f = 0; f < n_frag; ++f) {
-    const int nf = n_orb[f];
-    const int64_t n2 = (int64_t)nf * nf;
-    const int64_t sq = n2 * np;  // q stride of M
-    const double2* Cf = (const double2*)C[f];
-    double* trf = nullptr;
-    const bool want_tr = (ej_out || ek_out) && gamma && gamma[f];
-    if (want_tr) {
-      trf = (double*)h->ensure("traces", sizeof(double) * (8 + 4 * (size_t)n2));
-      if (!trf) return fail(h, ISDF_ERR_OOM, "traces workspace");
-    }
-    if (!mixed) {
+  // The fragments go one after the other on the stream with no host
+  // synchronisation in between: each writes its traces into its slot of a
+  // device array, and the bounded-wait error word of the tensor-core kernels is
+  // read once at the end.
+  const bool any_tr = (ej_out || ek_out) && gamma;
+  ENSURE(trall, double, "frag_traces", 4 * (size_t)n_frag);
+  ENSURE(tcw, int, "tc_words", 4);
+  CK(cudaMemsetAsync(trall, 0, sizeof(double) * 4 * (size_t)n_frag, h->st));
+  CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
+  if (!mixed) {
+    for (int f = 0; f < n_frag; ++f) {
+      const int nf = n_orb[f];
+      const int64_t n2 = (int64_t)nf * nf;
+      const int64_t sq = n2 * np;  // q stride of M
+      const double2* Cf = (const double2*)C[f];
+      double* trf = trall + 4 * (int64_t)f;
+      double2* trpart = nullptr;
+      const bool want_tr = any_tr && gamma[f];
+      if (want_tr) {
+        trpart = (double2*)h->ensure("frag_traces_part", sizeof(double2) * 2 * (size_t)n2);
+        if (!trpart) return fail(h, ISDF_ERR_OOM, "traces workspace");
+      }
       const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
       double2* X = (double2*)h->buf("X");
       ENSURE(Lw, double2, "frag_Lw", (size_t)nk * pp);
@@ -856,125 +986,200 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         if (h->q_sym) CK(eri_swapconj_sym(h->st, E, nf));
       }
       if (eri_out && eri_out[f]) CK(eri_permute(h->st, E, nf, 1.0 / nk, (double2*)eri_out[f]));
-      if (want_tr) CK(eri_traces(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf));
+      if (want_tr) CK(eri_traces(h->st, E, nf, 1.0 / nk, (const double2*)gamma[f], trf, trpart));
+    }
+  } else {
+    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+    float2* Xf = (float2*)h->buf("X_f");
+    // B = M L on the tensor cores (four exact slices) when the 2 r_q gathered
+    // columns fit their exact accumulation, else on the compensated SIMT GEMM
+    const bool tc_ml = mlgemm_tc_supported(rp);
+    float2* Lwf = nullptr;
+    void* lsl = nullptr;
+    int* lexp = nullptr;
+    if (tc_ml) {
+      lsl = h->ensure_evict("frag_Lsl", mlgemm_tc_lslice_bytes(nk, rp, nj));
+      lexp = (int*)h->ensure_evict("frag_Lexp", sizeof(int) * (size_t)nk * mlgemm_tc_nj_pad(nj));
+      if (!lsl || !lexp) return fail(h, ISDF_ERR_OOM, "device allocation of the slices of L failed");
+      CK(mlgemm_tc_prepare(h->st, Lq, swd, nk, np, permPi, rankPi, rp, nj, lsl, lexp));
     } else {
-      const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-      float2* Xf = (float2*)h->buf("X_f");
-      // B = M L on the tensor cores (four exact slices) when the 2 r_q gathered
-      // columns fit their exact accumulation, else on the compensated SIMT GEMM
-      const bool tc_ml = mlgemm_tc_supported(rp);
-      float2* Lwf = nullptr;
-      void* lsl = nullptr;
-      int* lexp = nullptr;
-      if (tc_ml) {
-        lsl = h->ensure_evict("frag_Lsl", mlgemm_tc_lslice_bytes(nk, rp, nj));
-        lexp = (int*)h->ensure_evict("frag_Lexp", sizeof(int) * (size_t)nk * mlgemm_tc_nj_pad(nj));
-        if (!lsl || !lexp) return fail(h, ISDF_ERR_OOM, "device allocation of the slices of L failed");
-      } else {
-        Lwf = (float2*)h->ensure_evict("frag_Lwf", sizeof(float2) * (size_t)nk * pp);
-        if (!Lwf) return fail(h, ISDF_ERR_OOM, "device allocation of frag_Lwf failed");
+      Lwf = (float2*)h->ensure_evict("frag_Lwf", sizeof(float2) * (size_t)nk * pp);
+      if (!Lwf) return fail(h, ISDF_ERR_OOM, "device allocation of frag_Lwf failed");
+      CK(scale_blocks_f(h->st, Lq, pp, nk, swd, Lwf));
+    }
+    ENSURE(qslot_d, int, "frag_qslot", nk);
+    CK(cudaMemcpyAsync(qslot_d, slot.data(), nk * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    const int64_t ldB = tc_ml ? nj : np;
+    // Groups of fragments contracted together: fragments whose lower triangle of
+    // 128 x 128 tiles fills few waves of the GPU go with others of their kind,
+    // their rows stacked (each block padded to a tile boundary) so that one launch
+    // of each kernel covers the group and the tiles of all its diagonal blocks;
+    // a group never needs more scratch than the largest fragment alone.
+    const std::vector<std::vector<int>> groups = fragment_groups(n_frag, n_orb, nk, nS, np);
+    for (const auto& grp : groups) {
+      // rows of each fragment inside the stacked block; padding rows are zero
+      std::vector<int64_t> row0(grp.size());
+      int64_t rows = 0;
+      for (size_t i = 0; i < grp.size(); ++i) {
+        const int64_t n2f = (int64_t)n_orb[grp[i]] * n_orb[grp[i]];
+        row0[i] = rows;
+        rows += (i + 1 < grp.size()) ? (n2f + 127) / 128 * 128 : n2f;
       }
-      ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nf);
-      ENSURE(T, float2, "frag_T", (size_t)nk * np * nf);
-      ENSURE(M, float2, "frag_Mf", (size_t)nk * sq);
-      ENSURE(E, double2, "frag_E", (size_t)n2 * n2);
+      const int64_t sq = rows * np;  // q stride of M
+      int nfmax = 0;
+      double flops3 = 0.0, flops4 = 0.0, flops5 = 0.0;
+      for (int f : grp) {
+        const int64_t n2f = (int64_t)n_orb[f] * n_orb[f];
+        nfmax = std::max(nfmax, (int)n_orb[f]);
+        flops3 += frag_m_flops(nk, np, n_orb[f], nao, km);
+        flops4 += 8.0 * (double)n2f * (tc_ml ? sum_rn : (double)np * sum_nv);
+        flops5 += 2.0 * (double)n2f * (double)(n2f + 1) * sum_nv;
+      }
+      const int64_t n2max = (int64_t)nfmax * nfmax;
+      ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nfmax);
+      ENSURE(T, float2, "frag_T", (size_t)nk * np * nfmax);
+      // real pair rows Z(R) of the time-reversal basis, and M^q (then B^q) of the
+      // q of the sum, stored by their position in it
+      ENSURE(Zr, float, "frag_Zr", (size_t)nk * sq);
+      ENSURE(M, float2, "frag_Mf", (size_t)nS * sq);
+      ENSURE(trpart, double2, "frag_traces_part", std::max<size_t>(2 * (size_t)n2max, syrk_tc_eri_part_count()));
+      // tiles of every fragment's diagonal block, in the autotuned band order
       std::vector<int2>& tl = h->tiles_host;
-      syrk_tc_tiles(n2, tl, h->tile_of_host);
-      pair_orbits(nf, h->orb_host);
-      const int norb = (int)h->orb_host.size();
+      std::vector<int>& tof = h->tile_of_host;
+      std::vector<int64_t> tof_off(grp.size());
+      auto build_tiles = [&](int band) {
+        tl.clear();
+        tof.clear();
+        for (size_t i = 0; i < grp.size(); ++i) {
+          const int64_t n2f = (int64_t)n_orb[grp[i]] * n_orb[grp[i]];
+          std::vector<int2> t;
+          std::vector<int> of;
+          syrk_tc_tiles(n2f, t, of, band);
+          const int t0 = (int)(row0[i] / 128), base = (int)tl.size();
+          for (const int2& x : t) tl.push_back(make_int2(x.x + t0, x.y + t0));
+          tof_off[i] = (int64_t)tof.size();
+          for (int v : of) tof.push_back(v < 0 ? -1 : v + base);
+        }
+      };
+      build_tiles(12);
+      std::vector<int2>& orb = h->orb_host;
+      std::vector<int64_t> orb_off(grp.size());
+      orb.clear();
+      for (size_t i = 0; i < grp.size(); ++i) {
+        std::vector<int2> o;
+        pair_orbits(n_orb[grp[i]], o);
+        orb_off[i] = (int64_t)orb.size();
+        orb.insert(orb.end(), o.begin(), o.end());
+      }
       // B^q = w_q^{1/2} M^q L^q overwrites M^q (row pitch nj on the tensor-core
       // path, np through Bc on the SIMT path), qc q-points at a time; E' then
-      // takes the rows of B^q of S in chunks of qc q-points (fp16 slices of
-      // 2 qc nj columns).  qc fits both slice buffers in the workspace limit.
-      const int64_t ldB = tc_ml ? nj : np;
-      const size_t per_q = std::max(syrk_tc_split_bytes(n2, nj), tc_ml ? mlgemm_tc_split_bytes(n2, rp, 1) : 0);
+      // takes the rows of B^q in chunks of qc positions (fp16 slices of 2 qc nj
+      // columns).  qc fits both slice buffers in the workspace limit.
+      const size_t per_q = std::max(syrk_tc_split_bytes(rows, nj), tc_ml ? mlgemm_tc_split_bytes(rows, rp, 1) : 0);
       const int qc = (int)std::max<int64_t>(1, std::min<int64_t>(nS, (int64_t)(h->split_budget / per_q)));
       ENSURE(split, uint8_t, "tc_split",
-             std::max(syrk_tc_split_bytes(n2, (int64_t)qc * nj), tc_ml ? mlgemm_tc_split_bytes(n2, rp, qc) : 0));
+             std::max(syrk_tc_split_bytes(rows, (int64_t)qc * nj), tc_ml ? mlgemm_tc_split_bytes(rows, rp, qc) : 0));
       float2* Bc = nullptr;
       if (!tc_ml) {
         Bc = (float2*)h->ensure_evict("frag_Bc", sizeof(float2) * (size_t)qc * sq);
         if (!Bc) return fail(h, ISDF_ERR_OOM, "device allocation of frag_Bc failed");
       }
-      ENSURE(rexp, int, "tc_rowexp", n2);
+      ENSURE(rexp, int, "tc_rowexp", rows);
       ENSURE(tiles_d, int2, "tc_tiles", tl.size());
-      ENSURE(tile_of_d, int, "tc_tile_of", h->tile_of_host.size());
-      ENSURE(orb_d, int2, "tc_orbits", norb);
+      ENSURE(tile_of_d, int, "tc_tile_of", tof.size());
+      ENSURE(orb_d, int2, "tc_orbits", orb.size());
       ENSURE(ws, uint8_t, "tc_ws", syrk_tc_ws_bytes((int64_t)tl.size()));
-      ENSURE(tcw, int, "tc_words", 4);
       CK(cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
-      CK(cudaMemcpyAsync(tile_of_d, h->tile_of_host.data(), h->tile_of_host.size() * sizeof(int),
-                         cudaMemcpyHostToDevice, h->st));
-      CK(cudaMemcpyAsync(orb_d, h->orb_host.data(), norb * sizeof(int2), cudaMemcpyHostToDevice, h->st));
-      CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
-      if (f == 0) {
-        if (tc_ml)
-          CK(mlgemm_tc_prepare(h->st, Lq, swd, nk, np, permPi, rankPi, rp, nj, lsl, lexp));
-        else
-          CK(scale_blocks_f(h->st, Lq, pp, nk, swd, Lwf));
+      CK(cudaMemcpyAsync(tile_of_d, tof.data(), tof.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+      CK(cudaMemcpyAsync(orb_d, orb.data(), orb.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
+      {
+        StageTimer stt(h, 3, flops3);
+        for (size_t i = 0; i < grp.size(); ++i) {
+          const int f = grp[i], nf = n_orb[f];
+          const int64_t n2f = (int64_t)nf * nf;
+          CK(z2c(h->st, (const double2*)C[f], Cff, (int64_t)nk * nao * nf));
+          CK(cgemm(h->st, 'N', 'N', np, nf, nao, one, Xf, nao, (int64_t)np * nao, Cff, nf, (int64_t)nao * nf, zero,
+                   T, nf, (int64_t)np * nf, nk));
+          CK(kdft_cols_f(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.f));
+          // pair rows in the time-reversal basis are real: Z(R) in FP32
+          CK(pair_products_real_f(h->st, T, nk, np, nf, Zr, row0[i], rows));
+          const int64_t pad = (i + 1 < grp.size()) ? row0[i + 1] - row0[i] - n2f : 0;
+          if (pad > 0)
+            CK(cudaMemset2DAsync(Zr + (row0[i] + n2f) * np, sizeof(float) * (size_t)sq, 0,
+                                 sizeof(float) * (size_t)(pad * np), nk, h->st));
+        }
+        // the R -> q DFT keeps only the q of the sum (M^{-q} = conj(M^q))
+        CK(kdft_real_f(h->st, Zr, M, sq, km, +1, 1.f / nk, qslot_d));
       }
       {
-        StageTimer stt(h, 3, frag_m_flops(nk, np, nf, nao, km));
-        CK(z2c(h->st, Cf, Cff, (int64_t)nk * nao * nf));
-        CK(cgemm(h->st, 'N', 'N', np, nf, nao, one, Xf, nao, (int64_t)np * nao, Cff, nf, (int64_t)nao * nf, zero, T,
-                 nf, (int64_t)np * nf, nk));
-        CK(kdft_cols_f(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.f));
-        CK(pair_products_f(h->st, T, nk, np, nf, M));
-        CK(kdft_cols_f(h->st, M, n2 * np, km, +1, +1, 0, 1.f / nk));
-      }
-      {
-        StageTimer stt(h, 4, 8.0 * (double)n2 * (tc_ml ? sum_rn : (double)np * sum_nv));
+        StageTimer stt(h, 4, flops4);
         if (tc_ml) {
           // row exponents of the gathered M over the q of the sum, then B^q = M^q L^q
           // over M^q, q-chunk by q-chunk
-          CK(mlgemm_tc_rowscale(h->st, M, sq, np, qmap, nS, permPi, rankPi, rp, n2, rexp));
+          CK(mlgemm_tc_rowscale(h->st, M, sq, np, qmap, nS, permPi, rankPi, rp, rows, rexp));
           for (int j0 = 0; j0 < nS; j0 += qc)
-            CK(mlgemm_tc_chunk(h->st, M, sq, qmap, n2, np, permPi, rankPi, rp, nj, j0, std::min(qc, nS - j0), rexp,
-                               split, lsl, lexp, nk, tcw + 1));
+            CK(mlgemm_tc_chunk(h->st, M, sq, qmap, rows, np, permPi, rankPi, rp, nj, j0, std::min(qc, nS - j0),
+                               rexp, split, lsl, lexp, nk, tcw + 1));
         } else {
+          // consecutive q of a run sit at consecutive positions
           for (const auto& r : runs)
             for (int q0 = r.first; q0 < r.first + r.second; q0 += qc) {
               const int nq = std::min(qc, r.first + r.second - q0);
-              CK(cgemm(h->st, 'N', 'N', (int)n2, np, np, one, M + q0 * sq, np, sq, Lwf + q0 * pp, np, pp, zero, Bc,
+              const int64_t j = slot[q0];
+              CK(cgemm(h->st, 'N', 'N', (int)rows, np, np, one, M + j * sq, np, sq, Lwf + q0 * pp, np, pp, zero, Bc,
                        np, sq, nq));
-              CK(cudaMemcpyAsync(M + q0 * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice,
+              CK(cudaMemcpyAsync(M + j * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice,
                                  h->st));
             }
         }
       }
       {
         // E' = c sum_{q in S} [Re R^q, Im R^q][Re R^q, Im R^q]^T over the rows of B^q in the
-        // time-reversal basis (real symmetric, lower-triangle tiles), then E = W E' W^H;
-        // c = 2 with the pairing (S about half the mesh), 1 over every q
-        StageTimer stt(h, 5, 2.0 * (double)n2 * (double)(n2 + 1) * sum_nv);
-        CK(syrk_tc_rowscale(h->st, M, sq, ldB, nj, qmap, nS, orb_d, nf, rexp));
+        // time-reversal basis (real symmetric, lower-triangle tiles of each diagonal block),
+        // then E = W E' W^H per fragment; c = 2 with the pairing, 1 over every q
+        StageTimer stt(h, 5, flops5);
+        CK(syrk_tc_rowscale(h->st, M, sq, ldB, nj, nullptr, nS, rows, rexp));
+        const int nq0 = std::min(qc, nS);
+        const TileSchedule sch = tuned_schedule(h, (int64_t)tl.size(), [&](int cfg, int b) -> int {
+          build_tiles(b);
+          if (cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st) !=
+              cudaSuccess)
+            return -1;
+          return syrk_tc_chunk(h->st, M, sq, ldB, nj, nullptr, rows, 0, nq0, rexp, split, tiles_d, (int)tl.size(),
+                               ws, 0, tcw + 1, cfg) == cudaSuccess ? 0 : -1;
+        });
+        if (sch.band < 0) return fail(h, ISDF_ERR_CUDA, "tile-schedule tuning launch failed");
+        build_tiles(sch.band);
+        CK(cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(tile_of_d, tof.data(), tof.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
         for (int j0 = 0; j0 < nS; j0 += qc) {
           const int nq = std::min(qc, nS - j0);
-          CK(syrk_tc_chunk(h->st, M, sq, ldB, nj, qmap, orb_d, nf, j0, nq, rexp, split, tiles_d, (int)tl.size(), ws,
-                           j0 > 0, tcw + 1));
+          CK(syrk_tc_chunk(h->st, M, sq, ldB, nj, nullptr, rows, j0, nq, rexp, split, tiles_d, (int)tl.size(), ws,
+                           j0 > 0, tcw + 1, sch.cfg));
         }
-        CK(syrk_tc_finish(h->st, ws, (int)tl.size(), tile_of_d, orb_d, nf, rexp, (h->q_sym ? 2.0 : 1.0) / nk, E));
+        // E = W E' W^H per fragment, written straight to the caller's ERIs (chemist's
+        // order) with the FP64 traces accumulated on the way
+        for (size_t i = 0; i < grp.size(); ++i) {
+          const int f = grp[i];
+          CK(syrk_tc_finish_eri(h->st, ws, (int)tl.size(), tile_of_d + tof_off[i], orb_d + orb_off[i], n_orb[f],
+                                rexp + row0[i], (h->q_sym ? 2.0 : 1.0) / nk,
+                                eri_out ? (float2*)eri_out[f] : nullptr,
+                                any_tr ? (const double2*)gamma[f] : nullptr, trpart, trall + 4 * (int64_t)f));
+        }
       }
-      if (eri_out && eri_out[f]) CK(eri_permute_zc(h->st, E, nf, 1.0, (float2*)eri_out[f]));
-      if (want_tr) CK(eri_traces(h->st, E, nf, 1.0, (const double2*)gamma[f], trf));
-      int tc_err = 0;
-      CK(cudaMemcpyAsync(&tc_err, tcw + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-      CK(cudaStreamSynchronize(h->st));
-      if (tc_err != 0)
-        return fail(h, ISDF_ERR_TIMEOUT, "tensor-core contraction: bounded device wait expired (code %d)", tc_err);
-    }
-    if (want_tr) {
-      double hv[4];
-      CK(cudaMemcpyAsync(hv, trf, sizeof(hv), cudaMemcpyDeviceToHost, h->st));
-      CK(cudaStreamSynchronize(h->st));
-      if (ej_out) ej_out[f] = hv[0];
-      if (ek_out) ek_out[f] = hv[1];
-    } else {
-      if (ej_out) ej_out[f] = 0.0;
-      if (ek_out) ek_out[f] = 0.0;
     }
   }
+  std::vector<double> hv(4 * (size_t)n_frag, 0.0);
+  int tc_err = 0;
+  if (any_tr) CK(cudaMemcpyAsync(hv.data(), trall, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&tc_err, tcw + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  if (tc_err != 0)
+    return fail(h, ISDF_ERR_TIMEOUT, "tensor-core contraction: bounded device wait expired (code %d)", tc_err);
+  for (int f = 0; f < n_frag; ++f) {
+    if (ej_out) ej_out[f] = hv[4 * (size_t)f];
+    if (ek_out) ek_out[f] = hv[4 * (size_t)f + 1];
+  }
   return ISDF_OK;
 }
 
@@ -1068,8 +1273,14 @@ int isdf_sos_polarizability(isdf_handle* h, const void* C, int n_mo, int n_occ, 
            Go, np, pp, nk));
   CK(zgemm(h->st, 'N', 'C', np, np, nvir, one, Yv, nvir, (int64_t)np * nvir, Y + n_occ, n_mo, (int64_t)np * n_mo,
            zero, Gv, np, pp, nk));
-  // chi^Q_{IK} = sum_k Go^k_{KI} Gv^{k-Q}_{IK} (Eq. 13)
-  CK(chi_kconv(h->st, Go, Gv, h->cell.kmesh, np, chi));
+  // chi^Q_{IK} = sum_k Go^k_{KI} Gv^{k-Q}_{IK} (Eq. 13) by the convolution theorem, as
+  // Algorithm 1 does for Pi^q: with hat(a)(R) = sum_k a(k) e^{+ik.R} and
+  // check(b)(R) = sum_k b(k) e^{-ik.R},  chi = (1/Nk) DFT_-( hat(Go)^T o check(Gv) )
+  const KMesh km{{h->cell.kmesh[0], h->cell.kmesh[1], h->cell.kmesh[2]}};
+  CK(kdft_cols(h->st, Go, pp, km, +1, +1, 0, 1.0));
+  CK(kdft_cols(h->st, Gv, pp, km, -1, -1, 0, 1.0));
+  CK(hadamard_t(h->st, Go, Gv, np, nk, chi));
+  CK(kdft_cols(h->st, chi, pp, km, -1, -1, 0, 1.0 / nk));
   if (s_out) {
     // S = Nk^2 sum_Q tr[conj(V^Q) chi^Q conj(V^Q) (chi^{-Q})^T], V^Q = L^Q L^Q^H (Eq. 12)
     CK(zgemm(h->st, 'N', 'C', np, np, np, one, Lq, np, pp, Lq, np, pp, zero, Vq, np, pp, nk));
@@ -1126,6 +1337,37 @@ int isdf_set_time_reversal(isdf_handle* h, int enable) {
   if (!h) return ISDF_ERR_ARG;
   h->q_sym = (enable != 0);
   return ISDF_OK;
+}
+
+int isdf_set_autotune(isdf_handle* h, int enable) {
+  if (!h) return ISDF_ERR_ARG;
+  h->autotune = (enable != 0);
+  return ISDF_OK;
+}
+
+int isdf_set_tile_schedule(isdf_handle* h, int pipeline, int band) {
+  if (!h) return ISDF_ERR_ARG;
+  if ((pipeline != 0 && pipeline != 1) || band < 1 || band > 64)
+    return fail(h, ISDF_ERR_ARG, "tile schedule: pipeline must be 0 or 1 and band in [1, 64]");
+  h->autotune = false;
+  h->fixed_cfg = pipeline;
+  h->fixed_band = band;
+  return ISDF_OK;
+}
+
+int isdf_autotune_report(const isdf_handle* h, char* buf, size_t len) {
+  if (!h || !buf || len == 0) return ISDF_ERR_ARG;
+  std::string r = "[";
+  for (size_t i = 0; i < h->tune_log.size(); ++i) {
+    const auto& e = h->tune_log[i];
+    char b[200];
+    snprintf(b, sizeof(b), "%s{\"tiles\": %lld, \"pipeline\": %d, \"band\": %d, \"ms\": [%.3f, %.3f, %.3f, %.3f]}",
+             i ? ", " : "", (long long)e.ntiles, e.cfg, e.band, e.ms[0], e.ms[1], e.ms[2], e.ms[3]);
+    r += b;
+  }
+  r += "]";
+  snprintf(buf, len, "%s", r.c_str());
+  return r.size() < len ? ISDF_OK : ISDF_ERR_ARG;
 }
 
 int isdf_set_workspace_limit(isdf_handle* h, uint64_t bytes) {

@@ -317,6 +317,88 @@ __global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, i
   }
 }
 
+// DFT along the k-mesh of real columns, out of place, keeping the q with
+// qslot[q] >= 0:  out[qslot[q]][col] = scale sum_k e^{s 2 pi i m_q.m_k/n} in[k][col].
+// The real pair rows of the time-reversal basis give M^{-q} = conj(M^q), so
+// the half set of q in qslot carries all of it.  Two real columns x, y share
+// one complex working column z = x + i y (a block holds 2 ct real columns, so
+// each k-row of the input is read 2 ct floats at a time); after the transform
+// X(q) = (Z(q) + conj(Z(-q)))/2 and Y(q) = (Z(q) - conj(Z(-q)))/(2i).
+template <typename T, int L>
+__global__ void __launch_bounds__(256) kdft_real_cubic_kernel(const typename CT<T>::R* __restrict__ in,
+                                                              T* __restrict__ out, int64_t ncol, int lct, int padk,
+                                                              const int* __restrict__ qslot, Twiddles16 tw,
+                                                              double scale) {
+  using R = typename CT<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  __shared__ R twc[16], tws[16];
+  for (int t = threadIdx.x; t < 16; t += blockDim.x) {
+    twc[t] = (R)tw.c[0][t];
+    tws[t] = (R)tw.s[0][t];
+  }
+  constexpr int nk = L * L * L;
+  const int ct = 1 << lct;
+  const int64_t c0 = (int64_t)blockIdx.x << (lct + 1);  // 2 ct real columns per block
+  for (int e = threadIdx.x; e < nk * 2 * ct; e += blockDim.x) {
+    const int k = e >> (lct + 1), c2 = e & (2 * ct - 1);
+    const int64_t col = c0 + c2;
+    const R v = (col < ncol) ? in[(int64_t)k * ncol + col] : (R)0;
+    // column c2 < ct is the real part of working column c2, else the imaginary part of c2 - ct
+    R* w = reinterpret_cast<R*>(&s[cidx<T, L>(k, c2 & (ct - 1), lct, padk)]);
+    w[c2 >> lct] = v;
+  }
+  __syncthreads();
+  kmesh_dft_cubic<T, L>(s, lct, padk, twc, tws);
+  const R h = (R)(0.5 * scale);
+  for (int e = threadIdx.x; e < nk * 2 * ct; e += blockDim.x) {
+    const int k = e >> (lct + 1), c2 = e & (2 * ct - 1), c = c2 & (ct - 1);
+    const int64_t col = c0 + c2;
+    const int j = qslot[k];
+    if (col < ncol && j >= 0) {
+      const int m0 = k / (L * L), m1 = (k / L) % L, m2 = k % L;
+      const int km = (((L - m0) % L) * L + (L - m1) % L) * L + (L - m2) % L;
+      const T zq = s[cidx<T, L>(k, c, lct, padk)], zm = s[cidx<T, L>(km, c, lct, padk)];
+      out[(int64_t)j * ncol + col] = (c2 < ct) ? CT<T>::mk(h * (zq.x + zm.x), h * (zq.y - zm.y))
+                                               : CT<T>::mk(h * (zq.y + zm.y), h * (zm.x - zq.x));
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kdft_real_cols_kernel(const typename CT<T>::R* __restrict__ in,
+                                                             T* __restrict__ out, int64_t ncol, KMesh km, int ct,
+                                                             const int* __restrict__ qslot, Twiddles16 tw,
+                                                             double scale) {
+  using R = typename CT<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  __shared__ R twc[48], tws[48];
+  for (int t = threadIdx.x; t < 48; t += blockDim.x) {
+    twc[t] = (R)tw.c[t / 16][t % 16];
+    tws[t] = (R)tw.s[t / 16][t % 16];
+  }
+  const int nk = km.n[0] * km.n[1] * km.n[2];
+  const int64_t c0 = (int64_t)blockIdx.x * ct;
+  for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+    const int k = e / ct, c = e % ct;
+    const int64_t col = c0 + c;
+    const R v = (col < ncol) ? in[(int64_t)k * ncol + col] : (R)0;
+    s[e] = CT<T>::mk(v, 0);
+  }
+  __syncthreads();
+  kmesh_dft_smem<T>(s, ct, km.n, twc, tws);
+  for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+    const int k = e / ct, c = e % ct;
+    const int64_t col = c0 + c;
+    const int j = qslot[k];
+    if (col < ncol && j >= 0) {
+      const T v = s[e];
+      out[(int64_t)j * ncol + col] = CT<T>::mk(v.x * (R)scale, v.y * (R)scale);
+    }
+  }
+}
+
 // Row padding of the cubic k-DFT's shared layout.  One 128-byte phase of a
 // shared access serves G = 128 / sizeof(T) lanes; with ct < G columns per row
 // those lanes span G / ct lines.  Along the stride-1 axis consecutive lines
@@ -346,6 +428,26 @@ cudaError_t kdft_cubic_launch(cudaStream_t st, T* data, int64_t ncol, int mode, 
   const int64_t nblk = (ncol + (1 << lct) - 1) >> lct;
   if (nblk > 2147483647LL) return cudaErrorInvalidValue;
   kdft_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, lct, padk, mode, t1, t2, scale);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, int L>
+cudaError_t kdft_real_cubic_launch(cudaStream_t st, const typename CT<T>::R* in, T* out, int64_t ncol,
+                                   const Twiddles16& tw, double scale, const int* qslot) {
+  constexpr int nk = L * L * L;
+  int lct = 0;
+  while (lct < 5 && ((int64_t)nk * sizeof(T) << (lct + 1)) <= 65536) ++lct;
+  const int padk = kdft_cubic_pad(L, 1 << lct, (int)sizeof(T));
+  const size_t smem = ((size_t)nk << lct) * sizeof(T) + (size_t)(nk / L) * padk * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kdft_real_cubic_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t nblk = (ncol + (2 << lct) - 1) >> (lct + 1);  // 2 ct real columns per block
+  if (nblk > 2147483647LL) return cudaErrorInvalidValue;
+  kdft_real_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(in, out, ncol, lct, padk, qslot, tw, scale);
   count_launch();
   return cudaGetLastError();
 }
@@ -425,6 +527,41 @@ cudaError_t kdft_launch(cudaStream_t st, T* data, int64_t ncol, KMesh km, int s1
   if (nblk > 2147483647LL) return cudaErrorInvalidValue;
   kdft_cols_kernel<T><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, km, ct, mode,
                                                          make_tw(km.n, s1), make_tw(km.n, s2), scale);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kdft_real_launch(cudaStream_t st, const typename CT<T>::R* in, T* out, int64_t ncol, KMesh km, int s,
+                             double scale, const int* qslot) {
+  const int nk = km.n[0] * km.n[1] * km.n[2];
+  for (int a = 0; a < 3; ++a)
+    if (km.n[a] < 1 || km.n[a] > 16) return cudaErrorInvalidValue;
+  if (ncol <= 0) return cudaSuccess;
+  const Twiddles16 tw = make_tw(km.n, s);
+  if (km.n[0] == km.n[1] && km.n[1] == km.n[2]) {
+    switch (km.n[0]) {
+      case 2: return kdft_real_cubic_launch<T, 2>(st, in, out, ncol, tw, scale, qslot);
+      case 3: return kdft_real_cubic_launch<T, 3>(st, in, out, ncol, tw, scale, qslot);
+      case 4: return kdft_real_cubic_launch<T, 4>(st, in, out, ncol, tw, scale, qslot);
+      case 6: return kdft_real_cubic_launch<T, 6>(st, in, out, ncol, tw, scale, qslot);
+      case 8: return kdft_real_cubic_launch<T, 8>(st, in, out, ncol, tw, scale, qslot);
+      case 10: return kdft_real_cubic_launch<T, 10>(st, in, out, ncol, tw, scale, qslot);
+      default: break;
+    }
+  }
+  int ct = (int)(65536 / ((int64_t)nk * sizeof(T)));
+  if (ct < 1) ct = 1;
+  if (ct > 32) ct = 32;
+  const size_t smem = (size_t)nk * ct * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kdft_real_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t nblk = (ncol + ct - 1) / ct;
+  if (nblk > 2147483647LL) return cudaErrorInvalidValue;
+  kdft_real_cols_kernel<T><<<(unsigned)nblk, 256, smem, st>>>(in, out, ncol, km, ct, qslot, tw, scale);
   count_launch();
   return cudaGetLastError();
 }
@@ -669,6 +806,58 @@ __global__ void __launch_bounds__(256) pair_kernel(const T* __restrict__ t, int 
   }
 }
 
+// Pair rows in the time-reversal basis, real:  for the pair o = (p, q), p < q
+// (lexicographic), row 2o = 2 Re(conj(t_p) t_q) and row 2o + 1 = 2 Im(conj(t_p) t_q)
+// (the combinations Z_(pq) + Z_(qp) and -i (Z_(pq) - Z_(qp))), and row 2P + p = |t_p|^2.
+// Zr[R][row][I]; same block structure as pair_kernel (one R and kPairP values of p per
+// block, 16-column tiles of t[R] through shared memory, I across threads).
+template <typename T>
+__global__ void __launch_bounds__(256) pair_real_kernel(const T* __restrict__ t, int np, int nf,
+                                                        typename CT<T>::R* __restrict__ Zr, int64_t row0,
+                                                        int64_t rows) {
+  using R = typename CT<T>::R;
+  extern __shared__ __align__(16) unsigned char pair_smem[];
+  T* ts = reinterpret_cast<T*>(pair_smem);  // [np][kPairQ + 1]
+  const int Rk = blockIdx.y, p0 = blockIdx.x * kPairP;
+  const int64_t P = (int64_t)nf * (nf - 1) / 2;
+  const T* tr = t + (int64_t)Rk * np * nf;
+  R* zr = Zr + ((int64_t)Rk * rows + row0) * np;
+  for (int q0 = p0; q0 < nf; q0 += kPairQ) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * kPairQ; e += blockDim.x) {
+      const int I = e / kPairQ, j = e % kPairQ, q = q0 + j;
+      T v;
+      v.x = 0;
+      v.y = 0;
+      if (q < nf) v = tr[(int64_t)I * nf + q];
+      ts[I * (kPairQ + 1) + j] = v;
+    }
+    __syncthreads();
+    const int nq = min(kPairQ, nf - q0);
+    for (int I = threadIdx.x; I < np; I += blockDim.x) {
+#pragma unroll
+      for (int pi = 0; pi < kPairP; ++pi) {
+        const int p = p0 + pi;
+        if (p >= nf) break;
+        const T a = tr[(int64_t)I * nf + p];
+        const int64_t o0 = (int64_t)p * nf - (int64_t)p * (p + 1) / 2 - p - 1;  // pair index of (p, q) is o0 + q
+        for (int j = 0; j < nq; ++j) {
+          const int q = q0 + j;
+          if (q < p) continue;
+          const T b = ts[I * (kPairQ + 1) + j];
+          if (q == p) {
+            zr[(2 * P + p) * np + I] = a.x * a.x + a.y * a.y;
+          } else {
+            const int64_t o = o0 + q;
+            zr[(2 * o) * np + I] = (R)2 * (a.x * b.x + a.y * b.y);      // 2 Re(conj(a) b)
+            zr[(2 * o + 1) * np + I] = (R)2 * (a.x * b.y - a.y * b.x);  // 2 Im(conj(a) b)
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 cudaError_t pair_launch(cudaStream_t st, const T* t, int nk, int np, int nf, T* Z) {
   if ((int64_t)nk * nf * np == 0) return cudaSuccess;
@@ -684,7 +873,33 @@ cudaError_t pair_launch(cudaStream_t st, const T* t, int nk, int np, int nf, T* 
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t pair_real_launch(cudaStream_t st, const T* t, int nk, int np, int nf, typename CT<T>::R* Zr,
+                             int64_t row0, int64_t rows) {
+  if ((int64_t)nk * nf * np == 0) return cudaSuccess;
+  if (nk > 65535) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)np * (kPairQ + 1) * sizeof(T);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(pair_real_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  pair_real_kernel<T><<<dim3((nf + kPairP - 1) / kPairP, nk), 256, smem, st>>>(t, np, nf, Zr, row0, rows);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t kdft_real_f(cudaStream_t st, const float* in, float2* out, int64_t ncol, KMesh km, int s, float scale,
+                        const int* qslot) {
+  return kdft_real_launch<float2>(st, in, out, ncol, km, s, scale, qslot);
+}
+cudaError_t pair_products_real_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float* Zr, int64_t row0,
+                                 int64_t rows) {
+  if (row0 < 0 || row0 + (int64_t)nf * nf > rows) return cudaErrorInvalidValue;
+  return pair_real_launch<float2>(st, t, nk, np, nf, Zr, row0, rows);
+}
 
 cudaError_t kdft_cols(cudaStream_t st, double2* data, int64_t ncol, KMesh km, int s1, int s2,
                       int mode, double scale) {
@@ -715,9 +930,6 @@ void grid_twiddles(const int mesh[3], double2* host192) {
 }
 cudaError_t pair_products(cudaStream_t st, const double2* t, int nk, int np, int nf, double2* Z) {
   return pair_launch<double2>(st, t, nk, np, nf, Z);
-}
-cudaError_t pair_products_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float2* Z) {
-  return pair_launch<float2>(st, t, nk, np, nf, Z);
 }
 
 }  // namespace isdf

@@ -189,27 +189,6 @@ __global__ void scale_cols_kernel(const double2* __restrict__ y, int nk, int np,
   }
 }
 
-// chi[Q][I][K] = sum_k go[k][K][I] gv[k - Q][I][K]  (direct k-convolution on the mesh)
-__global__ void chi_kconv_kernel(const double2* __restrict__ go, const double2* __restrict__ gv, int n0, int n1,
-                                 int n2, int np, double2* __restrict__ chi) {
-  const int nk = n0 * n1 * n2;
-  const int64_t pp = (int64_t)np * np, total = (int64_t)nk * pp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int Q = (int)(e / pp);
-    const int I = (int)((e % pp) / np), K = (int)(e % np);
-    const int q0 = Q / (n1 * n2), q1 = (Q / n2) % n1, q2 = Q % n2;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k < nk; ++k) {
-      const int k0 = k / (n1 * n2), k1 = (k / n2) % n1, k2 = k % n2;
-      const int m = (((k0 - q0 + n0) % n0) * n1 + (k1 - q1 + n1) % n1) * n2 + (k2 - q2 + n2) % n2;
-      const double2 a = go[(int64_t)k * pp + (int64_t)K * np + I], b = gv[(int64_t)m * pp + (int64_t)I * np + K];
-      acc.x += a.x * b.x - a.y * b.y;
-      acc.y += a.x * b.y + a.y * b.x;
-    }
-    chi[e] = acc;
-  }
-}
-
 // part[Q] = Re sum_IJ t[Q][I][J] chi[-Q][I][J]  (one block per Q, fixed summation order)
 __global__ void __launch_bounds__(256) sos_trace_kernel(const double2* __restrict__ t, const double2* __restrict__ chi,
                                                         int n0, int n1, int n2, int np, double* __restrict__ part) {
@@ -260,8 +239,8 @@ cudaError_t eri_permute_zc(cudaStream_t st, const double2* E, int nf, double sca
   return cudaGetLastError();
 }
 
-// out2 must hold 4 doubles of device memory plus 2*nf*nf double2 of scratch after it
-// (passed as `part`).
+// out receives 4 doubles (E_J, E_K and their imaginary parts); part is 2*nf*nf double2
+// of scratch.
 template <typename T>
 static cudaError_t traces_impl(cudaStream_t st, const T* E, int nf, double scale, const double2* gamma,
                                double* out, double2* part) {
@@ -274,8 +253,7 @@ static cudaError_t traces_impl(cudaStream_t st, const T* E, int nf, double scale
 }
 
 cudaError_t eri_traces(cudaStream_t st, const double2* E, int nf, double scale, const double2* gamma,
-                       double* out) {
-  double2* part = reinterpret_cast<double2*>(out + 4);
+                       double* out, double2* part) {
   return traces_impl<double2>(st, E, nf, scale, gamma, out, part);
 }
 
@@ -305,12 +283,6 @@ cudaError_t scale_cols(cudaStream_t st, const double2* y, int nk, int np, int nm
                        double sgn_tau, double2* out) {
   if ((int64_t)nk * np * nc == 0) return cudaSuccess;
   scale_cols_kernel<<<nblocks((int64_t)nk * np * nc), 256, 0, st>>>(y, nk, np, nmo, c0, nc, eps, sgn_tau, out);
-  count_launch();
-  return cudaGetLastError();
-}
-cudaError_t chi_kconv(cudaStream_t st, const double2* go, const double2* gv, const int kmesh[3], int np, double2* chi) {
-  const int nk = kmesh[0] * kmesh[1] * kmesh[2];
-  chi_kconv_kernel<<<nblocks((int64_t)nk * np * np), 256, 0, st>>>(go, gv, kmesh[0], kmesh[1], kmesh[2], np, chi);
   count_launch();
   return cudaGetLastError();
 }

@@ -14,9 +14,11 @@
 // Gamma-centred, so V^{-q} = conj(V^q) and M^{-q}_{(qp)} = conj(M^q_{(pq)}), hence
 // E_{s(a) s(b)} = conj(E_ab) with s((pq)) = (qp).  That antiunitary symmetry fixes
 // the basis  u_(pq) = e_(pq) + e_(qp),  v_(pq) = i (e_(pq) - e_(qp))  (p < q)  and
-// e_(pp), so E is real in it.  With the rows of B^q taken in that basis,
-//     R_u = B_(pq) + B_(qp),   R_v = -i (B_(pq) - B_(qp)),   R_pp = B_(pp),
-// E' = sum_{all q} R^q R^q^H is real, i.e. E' = c sum_{q in S} [Re R^q, Im R^q] [Re R^q, Im R^q]^T
+// e_(pp), so E is real in it.  The pair products are formed in that basis
+// (rows u: 2 Re(conj(t_p) t_q), v: 2 Im(conj(t_p) t_q), pp: |t_p|^2, all real), so
+// the rows R^q of M^q and B^q = M^q L^q are already those of the basis, with
+// M^{-q} = conj(M^q); E' = sum_{all q} R^q R^q^H is real, i.e.
+//     E' = c sum_{q in S} [Re R^q, Im R^q] [Re R^q, Im R^q]^T
 // (c = 2 over the half set S of the time-reversal pairing, c = 1 over every q).
 // One real SYRK of n_f^2 rows replaces the complex HERK: half its real
 // products.  Only lower-triangle tiles are formed; the finish maps E' to E.
@@ -50,6 +52,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace isdf {
 
@@ -68,92 +71,6 @@ constexpr int NTHREADS = 192;
 constexpr int kChunkKB = 16;                // k-blocks per exact g0 chunk: 64 k-steps of 16
 constexpr int kP1 = 4;                      // chunks per g1 drain
 constexpr int kP2 = 16;                     // chunks per g2 drain
-constexpr unsigned long long kWaitNs = 4000000000ULL;  // bounded waits: 4 s of device time
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait for the phase of parity `parity`; false on timeout or if another
-// thread of the CTA already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* s_err, int* g_err,
-                                          int code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0) {
-      if (*s_err) return false;
-      if (global_ns() - t0 > kWaitNs) break;
-    }
-  }
-  *s_err = code;
-  atomicCAS(g_err, 0, code);
-  return false;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1024 bytes (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
-  const uint32_t a = smem_u32(p);
-  return (uint64_t)((a & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // Instruction descriptor of kind::f16: FP32 accumulate, fp16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -167,30 +84,35 @@ struct TileArgs {
   int* err;            // device error word
 };
 
+// Pipeline variants: BKt fp16 of K per stage row (64: 128-byte swizzle, 32: 64-byte
+// swizzle) and NST stages; a 1024-element exact chunk of g0 is 1024 / BKt k-blocks.
+template <int BKt, int NST>
 __global__ void __launch_bounds__(NTHREADS, 1)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
                    const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mB1,
                    const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, TileArgs args) {
+  constexpr int kA = BM * BKt * 2, kB = BN * BKt * 2, kStage = NSLICE * (kA + kB);
+  constexpr int kChunk = 1024 / BKt;  // k-blocks per exact g0 chunk
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // 1024-byte alignment of the shared-window address (128-byte swizzle atoms)
+  // 1024-byte alignment of the shared-window address (swizzle atoms)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* full = bars;                   // [STAGES]
-  uint64_t* empty = bars + STAGES;         // [STAGES]
-  uint64_t* accf = bars + 2 * STAGES;      // [2] chunk accumulated (per g0 buffer)
-  uint64_t* acce = bars + 2 * STAGES + 2;  // [2] g0 buffer drained
-  uint64_t* acce1 = bars + 2 * STAGES + 4; // g1 drained
-  uint64_t* acce2 = bars + 2 * STAGES + 5; // g2 drained
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NST * kStage);
+  uint64_t* full = bars;                   // [NST]
+  uint64_t* empty = bars + NST;         // [NST]
+  uint64_t* accf = bars + 2 * NST;      // [2] chunk accumulated (per g0 buffer)
+  uint64_t* acce = bars + 2 * NST + 2;  // [2] g0 buffer drained
+  uint64_t* acce1 = bars + 2 * NST + 4; // g1 drained
+  uint64_t* acce2 = bars + 2 * NST + 5; // g2 drained
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 6);
   volatile int* s_err = reinterpret_cast<volatile int*>(s_tmem + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int2 tile = args.tiles[blockIdx.x];
   const int nkb = args.nkb;
-  const int nchunks = (nkb + kChunkKB - 1) / kChunkKB;
+  const int nchunks = (nkb + kChunk - 1) / kChunk;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -219,24 +141,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const CUtensorMap* ma[3] = {&mA1, &mA2, &mA3};
       const CUtensorMap* mb[3] = {&mB1, &mB2, &mB3};
       for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES, r = kb / STAGES;
+        const int s = kb % NST, r = kb / NST;
         if (!mbar_wait(&empty[s], (r & 1) ^ 1, s_err, args.err, 1)) break;
-        uint8_t* st = smem + s * STAGE_BYTES;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        const int x = kb * BK;
+        uint8_t* st = smem + s * kStage;
+        mbar_expect_tx(&full[s], kStage);
+        const int x = kb * BKt;
 #pragma unroll
         for (int i = 0; i < NSLICE; ++i) {
-          tma_load_2d(st + i * A_BYTES, ma[i], &full[s], x, tile.x * BM);
-          tma_load_2d(st + NSLICE * A_BYTES + i * B_BYTES, mb[i], &full[s], x, tile.y * BN);
+          tma_load_2d(st + i * kA, ma[i], &full[s], x, tile.x * BM);
+          tma_load_2d(st + NSLICE * kA + i * kB, mb[i], &full[s], x, tile.y * BN);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES, r = kb / STAGES;
-        const int c = kb / kChunkKB;
-        const bool first_in_chunk = (kb % kChunkKB) == 0;
+        const int s = kb % NST, r = kb / NST;
+        const int c = kb / kChunk;
+        const bool first_in_chunk = (kb % kChunk) == 0;
         const bool reset1 = first_in_chunk && (c % kP1) == 0;
         const bool reset2 = first_in_chunk && (c % kP2) == 0;
         if (first_in_chunk) {
@@ -250,17 +172,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (!mbar_wait(&full[s], r & 1, s_err, args.err, 3)) break;
         tc_fence_after();
-        const uint8_t* st = smem + s * STAGE_BYTES;
+        const uint8_t* st = smem + s * kStage;
         uint64_t dA[3], dB[3];
 #pragma unroll
         for (int i = 0; i < NSLICE; ++i) {
-          dA[i] = sdesc_sw128(st + i * A_BYTES);
-          dB[i] = sdesc_sw128(st + NSLICE * A_BYTES + i * B_BYTES);
+          dA[i] = sdesc_k<BKt>(st + i * kA);
+          dB[i] = sdesc_k<BKt>(st + NSLICE * kA + i * kB);
         }
         const uint32_t g0 = tmem_base + (uint32_t)((c & 1) * BN), g1 = tmem_base + 2 * BN,
                        g2 = tmem_base + 3 * BN;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
+        for (int kk = 0; kk < BKt / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 fp16 = 32 bytes along K
           const uint32_t a0 = (first_in_chunk && kk == 0) ? 0u : 1u;
           const uint32_t a1 = (reset1 && kk == 0) ? 0u : 1u;
@@ -273,7 +195,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           umma_f16(g2, dA[2] + off, dB[0] + off, kIdesc, 1u);
         }
         umma_commit(&empty[s]);
-        if ((kb % kChunkKB) == kChunkKB - 1 || kb == nkb - 1) umma_commit(&accf[c & 1]);
+        if ((kb % kChunk) == kChunk - 1 || kb == nkb - 1) umma_commit(&accf[c & 1]);
       }
     }
   } else {
@@ -370,13 +292,6 @@ __device__ __forceinline__ float amax2(float2 v) { return fmaxf(fabsf(v.x), fabs
 // Exponent e with m 2^e in [64, 128) (0 for a zero or non-finite maximum).
 __device__ __forceinline__ int slice_exp(float m) { return (m > 0.f && isfinite(m)) ? 6 - ilogbf(m) : 0; }
 
-// Orbits of the swap (pq) <-> (qp): orb[o] = (p, q); o < P = n_f (n_f - 1)/2 are
-// the pairs p < q in lexicographic order, o = P + p the diagonal (p, p).  Rows
-// of R: pair o -> 2o (u) and 2o + 1 (v); diagonal p -> 2P + p.
-// u and v of a pair from x = B_(pq), y = B_(qp): u = x + y, v = -i (x - y).
-__device__ __forceinline__ float2 pair_u(float2 x, float2 y) { return make_float2(x.x + y.x, x.y + y.y); }
-__device__ __forceinline__ float2 pair_v(float2 x, float2 y) { return make_float2(x.y - y.y, y.x - x.x); }
-
 template <typename T>
 __device__ __forceinline__ T block_max(T v, T* sm) {
   for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -388,34 +303,16 @@ __device__ __forceinline__ T block_max(T v, T* sm) {
   return m;
 }
 
-// Row exponents of R over the whole sum (one block per orbit).
-__global__ void rrow_scale_kernel(BView B, const int2* __restrict__ orb, int nf, int64_t K,
-                                  int* __restrict__ row_exp) {
-  const int o = blockIdx.x, P = nf * (nf - 1) / 2;
-  const int2 pq = orb[o];
-  const int64_t a1 = (int64_t)pq.x * nf + pq.y, a2 = (int64_t)pq.y * nf + pq.x;
-  float mu = 0.f, mv = 0.f;
-  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-    const float2 x = B.at(a1, k);
-    if (o < P) {
-      const float2 y = B.at(a2, k);
-      mu = fmaxf(mu, amax2(pair_u(x, y)));
-      mv = fmaxf(mv, amax2(pair_v(x, y)));
-    } else {
-      mu = fmaxf(mu, amax2(x));
-    }
-  }
+// Row exponents of R over the whole sum (one block per row).  The rows of B^q
+// are those of the time-reversal basis: pair o = (p < q) -> rows 2o (u) and
+// 2o + 1 (v), diagonal p -> row 2P + p; R^q = [Re B^q, Im B^q].
+__global__ void rrow_scale_kernel(BView B, int64_t K, int* __restrict__ row_exp) {
+  const int64_t a = blockIdx.x;
+  float m = 0.f;
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) m = fmaxf(m, amax2(B.at(a, k)));
   __shared__ float sm[32];
-  mu = block_max(mu, sm);
-  mv = block_max(mv, sm);
-  if (threadIdx.x == 0) {
-    if (o < P) {
-      row_exp[2 * o] = slice_exp(mu);
-      row_exp[2 * o + 1] = slice_exp(mv);
-    } else {
-      row_exp[2 * P + (o - P)] = slice_exp(mu);
-    }
-  }
+  m = block_max(m, sm);
+  if (threadIdx.x == 0) row_exp[a] = slice_exp(m);
 }
 
 // Three integer slices of the (re, im) pair v 2^ex, written as half2 at S_i[at].
@@ -439,32 +336,16 @@ __device__ __forceinline__ void put3(float2 v, int ex, int64_t at, __half* __res
   *reinterpret_cast<__half2*>(S3 + at) = __halves2half2(h3[0], h3[1]);
 }
 
-// Slices of the R rows for the sum positions j0 .. j0 + nq - 1: row rho holds,
-// at columns 2 (jl nJ + J) and + 1, the (re, im) of R at (position j0 + jl, J);
+// Slices of the R rows for the sum positions j0 .. j0 + nq - 1: row a holds, at
+// columns 2 (jl nJ + J) and + 1, the (re, im) of B at (position j0 + jl, J);
 // columns beyond 2 nq nJ (up to the padded width K2) are zero.
-__global__ void rsplit_kernel(BView B, const int2* __restrict__ orb, int nf, int64_t j0, int nq, int64_t K2,
-                              const int* __restrict__ row_exp, __half* __restrict__ S1, __half* __restrict__ S2,
-                              __half* __restrict__ S3) {
-  const int no = nf * (nf + 1) / 2, P = nf * (nf - 1) / 2;
-  const int64_t half = K2 / 2, ncol = (int64_t)nq * B.nJ, total = (int64_t)no * half;
+__global__ void rsplit_kernel(BView B, int64_t n2, int64_t j0, int nq, int64_t K2, const int* __restrict__ row_exp,
+                              __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3) {
+  const int64_t half = K2 / 2, ncol = (int64_t)nq * B.nJ, total = n2 * half;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int o = (int)(e / half);
-    const int64_t c2 = e - (int64_t)o * half;
-    const int2 pq = orb[o];
-    const int64_t a1 = (int64_t)pq.x * nf + pq.y, a2 = (int64_t)pq.y * nf + pq.x;
-    float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
-    if (c2 < ncol) {
-      const int64_t k = j0 * B.nJ + c2;
-      x = B.at(a1, k);
-      if (o < P) y = B.at(a2, k);
-    }
-    if (o < P) {
-      put3(pair_u(x, y), row_exp[2 * o], (int64_t)(2 * o) * K2 + 2 * c2, S1, S2, S3);
-      put3(pair_v(x, y), row_exp[2 * o + 1], (int64_t)(2 * o + 1) * K2 + 2 * c2, S1, S2, S3);
-    } else {
-      const int64_t row = 2 * (int64_t)P + (o - P);
-      put3(x, row_exp[row], row * K2 + 2 * c2, S1, S2, S3);
-    }
+    const int64_t a = e / half, c2 = e - a * half;
+    const float2 x = (c2 < ncol) ? B.at(a, j0 * B.nJ + c2) : make_float2(0.f, 0.f);
+    put3(x, row_exp[a], a * K2 + 2 * c2, S1, S2, S3);
   }
 }
 
@@ -484,7 +365,9 @@ __device__ __forceinline__ double ep_val(const float* __restrict__ wh, const flo
 
 // E (complex128 n2 x n2, full) from E' = W^H E W: E = W E' W^H with the
 // unnormalised rows above, i.e. coefficients 1/2 (u) and +-i/2 (v) for pair
-// rows and 1 for diagonal rows.  One thread per orbit pair writes its 1, 2 or 4 entries.
+// rows and 1 for diagonal rows.  orb[o] = (p, q): o < P the pairs p < q in
+// lexicographic order (rows 2o, 2o + 1), o = P + p the diagonals (row 2P + p).
+// One thread per orbit pair writes its 1, 2 or 4 entries.
 __global__ void syrk_finish_kernel(const float* __restrict__ wh, const float* __restrict__ wl,
                                    const int* __restrict__ tile_of, int nt, const int2* __restrict__ orb, int nf,
                                    const int* __restrict__ row_exp, double scale, double2* __restrict__ E) {
@@ -524,6 +407,109 @@ __global__ void syrk_finish_kernel(const float* __restrict__ wh, const float* __
   }
 }
 
+// The same map with the chemist's permutation and the traces fused, so that E is
+// never stored: E_ab (a = (pq), b = (xy)) is (pq|yx), written to eri[p][q][y][x]
+// (complex64; eri may be NULL), and with gamma (may be NULL) each thread adds
+// gamma_pq gamma_yx E_ab to its J sum and gamma_px gamma_yq E_ab to its K sum.
+// Per-block partials go to part[blk] (J) and part[gridDim.x + blk] (K); a fixed
+// grid keeps the reduction order, and so the traces, reproducible.
+__device__ __forceinline__ void eri_put(float2* __restrict__ eri, const double2* __restrict__ gam, int nf, int p,
+                                        int q, int x, int y, double2 v, double2& aj, double2& ak) {
+  if (eri) eri[(((int64_t)p * nf + q) * nf + y) * nf + x] = make_float2((float)v.x, (float)v.y);
+  if (gam) {
+    const double2 gj = cmul(gam[(int64_t)p * nf + q], gam[(int64_t)y * nf + x]);
+    const double2 gk = cmul(gam[(int64_t)p * nf + x], gam[(int64_t)y * nf + q]);
+    cfma(aj, gj, v);
+    cfma(ak, gk, v);
+  }
+}
+
+__global__ void __launch_bounds__(256) syrk_eri_kernel(const float* __restrict__ wh, const float* __restrict__ wl,
+                                                       const int* __restrict__ tile_of, int nt,
+                                                       const int2* __restrict__ orb, int nf,
+                                                       const int* __restrict__ row_exp, double scale,
+                                                       float2* __restrict__ eri, const double2* __restrict__ gam,
+                                                       double2* __restrict__ part) {
+  const int no = nf * (nf + 1) / 2, P = nf * (nf - 1) / 2;
+  const int64_t total = (int64_t)no * no;
+  double2 aj = make_double2(0.0, 0.0), ak = make_double2(0.0, 0.0);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int o1 = (int)(e / no), o2 = (int)(e % no);
+    const int2 x1 = orb[o1], x2 = orb[o2];
+    const int p = x1.x, q = x1.y, x = x2.x, y = x2.y;
+    if (o1 < P && o2 < P) {
+      const int64_t iu = 2 * (int64_t)o1, ju = 2 * (int64_t)o2;
+      const double U = ep_val(wh, wl, tile_of, nt, iu, ju, row_exp, scale);
+      const double X = ep_val(wh, wl, tile_of, nt, iu, ju + 1, row_exp, scale);
+      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, ju, row_exp, scale);
+      const double Z = ep_val(wh, wl, tile_of, nt, iu + 1, ju + 1, row_exp, scale);
+      eri_put(eri, gam, nf, p, q, x, y, make_double2(0.25 * (U + Z), 0.25 * (Y - X)), aj, ak);   // (pq),(xy)
+      eri_put(eri, gam, nf, p, q, y, x, make_double2(0.25 * (U - Z), 0.25 * (X + Y)), aj, ak);   // (pq),(yx)
+      eri_put(eri, gam, nf, q, p, x, y, make_double2(0.25 * (U - Z), -0.25 * (X + Y)), aj, ak);  // (qp),(xy)
+      eri_put(eri, gam, nf, q, p, y, x, make_double2(0.25 * (U + Z), 0.25 * (X - Y)), aj, ak);   // (qp),(yx)
+    } else if (o1 < P) {
+      const int64_t iu = 2 * (int64_t)o1, j = 2 * (int64_t)P + (o2 - P);
+      const double U = ep_val(wh, wl, tile_of, nt, iu, j, row_exp, scale);
+      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, j, row_exp, scale);
+      eri_put(eri, gam, nf, p, q, x, x, make_double2(0.5 * U, 0.5 * Y), aj, ak);
+      eri_put(eri, gam, nf, q, p, x, x, make_double2(0.5 * U, -0.5 * Y), aj, ak);
+    } else if (o2 < P) {
+      const int64_t i = 2 * (int64_t)P + (o1 - P), ju = 2 * (int64_t)o2;
+      const double U = ep_val(wh, wl, tile_of, nt, i, ju, row_exp, scale);
+      const double X = ep_val(wh, wl, tile_of, nt, i, ju + 1, row_exp, scale);
+      eri_put(eri, gam, nf, p, p, x, y, make_double2(0.5 * U, -0.5 * X), aj, ak);
+      eri_put(eri, gam, nf, p, p, y, x, make_double2(0.5 * U, 0.5 * X), aj, ak);
+    } else {
+      const int64_t i = 2 * (int64_t)P + (o1 - P), j = 2 * (int64_t)P + (o2 - P);
+      eri_put(eri, gam, nf, p, p, x, x, make_double2(ep_val(wh, wl, tile_of, nt, i, j, row_exp, scale), 0.0), aj,
+              ak);
+    }
+  }
+  if (!gam) return;
+  __shared__ double2 sj[256], sk[256];
+  sj[threadIdx.x] = aj;
+  sk[threadIdx.x] = ak;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sj[threadIdx.x] = cadd(sj[threadIdx.x], sj[threadIdx.x + o]);
+      sk[threadIdx.x] = cadd(sk[threadIdx.x], sk[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sj[0];
+    part[gridDim.x + blockIdx.x] = sk[0];
+  }
+}
+
+// out4 = (E_J, E_K, Im E_J, Im E_K) from the per-block partials (one block, fixed order).
+__global__ void __launch_bounds__(256) eri_traces_final_kernel(const double2* __restrict__ part, int nblk,
+                                                               double* __restrict__ out4) {
+  __shared__ double2 sj[256], sk[256];
+  double2 aj = make_double2(0.0, 0.0), ak = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    aj = cadd(aj, part[i]);
+    ak = cadd(ak, part[nblk + i]);
+  }
+  sj[threadIdx.x] = aj;
+  sk[threadIdx.x] = ak;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sj[threadIdx.x] = cadd(sj[threadIdx.x], sj[threadIdx.x + o]);
+      sk[threadIdx.x] = cadd(sk[threadIdx.x], sk[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out4[0] = 0.5 * sj[0].x;
+    out4[1] = -0.25 * sk[0].x;
+    out4[2] = 0.5 * sj[0].y;
+    out4[3] = -0.25 * sk[0].y;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // B^q = M^q L^q on the tensor cores with four exact slices.
 //
@@ -552,10 +538,10 @@ constexpr int kMlMaxK = 640;                               // K' bound for exact
 constexpr uint32_t kIdescMl = (1u << 4) | ((uint32_t)(MBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 struct MlArgs {
-  float2* out;          // B: element (a, J) of the chunk's q-point ql at out[slot sq + a nj + J]
-  const int* qmap;      // slot of the chunk's q-points (indexed j0 + ql)
+  float2* out;          // B: element (a, J) of sum position j = j0 + ql at out[j sq + a nj + J]
+  const int* qmap;      // q of each sum position
   const int* row_exp;   // e_a, [n2]
-  const int* col_exp;   // f_qJ, [Nk][nj_pad] indexed by slot
+  const int* col_exp;   // f_qJ, [Nk][nj_pad] indexed by q
   int64_t sq;           // q stride of out
   int n2, nj, nj_pad, j0, nkb;
   int* err;
@@ -576,9 +562,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   volatile int* s_err = reinterpret_cast<volatile int*>(s_tmem + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = (2 * args.n2 + BM - 1) / BM;
-  const int ti = blockIdx.x % mt, tj = blockIdx.x / mt, ql = blockIdx.y;
-  const int slot = args.qmap ? args.qmap[args.j0 + ql] : args.j0 + ql;
+  // the output-column tiles of one row block are adjacent in launch order, so
+  // they run together and share the row block's slices through L2
+  const int ntj = args.nj_pad / MBN;
+  const int ti = blockIdx.x / ntj, tj = blockIdx.x % ntj, ql = blockIdx.y;
+  const int pos = args.j0 + ql;                      // position in the sum (storage of B)
+  const int slot = args.qmap ? args.qmap[pos] : pos;  // its q (slices and exponents of L)
   const int nkb = args.nkb;
 
   if (threadIdx.x == 0) {
@@ -693,7 +682,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("bar.sync 1, 128;" ::: "memory");
     if (okw) {
       const int t = threadIdx.x - 64;
-      float2* outq = args.out + (int64_t)slot * args.sq;
+      float2* outq = args.out + (int64_t)pos * args.sq;
       for (int idx = t; idx < (BM / 2) * MBN; idx += 128) {
         const int ar = idx / MBN, Jl = idx % MBN;
         const int64_t aa = (int64_t)ti * (BM / 2) + ar;
@@ -731,7 +720,8 @@ __device__ __forceinline__ void slice4(R v, __half& h1, __half& h2, __half& h3, 
 }
 
 // Row exponents of M over the gathered columns of the q-points of the sum:
-// max over positions Q < nS and c < r_q of |M^{q}_{a, perm_q[c]}|, q = qmap[Q].
+// max over positions Q < nS and c < r_q of |M^{q}_{a, perm_q[c]}|, q = qmap[Q],
+// with M^q stored at position Q.
 __global__ void mrow_scale_kernel(const float2* __restrict__ M, int64_t sq, int np, const int* __restrict__ qmap,
                                   int nS, const int* __restrict__ perm, const int* __restrict__ rank, int rp,
                                   int* __restrict__ row_exp) {
@@ -740,16 +730,16 @@ __global__ void mrow_scale_kernel(const float2* __restrict__ M, int64_t sq, int 
   for (int64_t k = threadIdx.x; k < (int64_t)nS * rp; k += blockDim.x) {
     const int Q = (int)(k / rp), c = (int)(k % rp);
     const int q = qmap[Q];
-    if (c < rank[q]) m = fmaxf(m, amax2(M[(int64_t)q * sq + a * np + perm[(int64_t)q * np + c]]));
+    if (c < rank[q]) m = fmaxf(m, amax2(M[(int64_t)Q * sq + a * np + perm[(int64_t)q * np + c]]));
   }
   __shared__ float sm[32];
   m = block_max(m, sm);
   if (threadIdx.x == 0) row_exp[a] = slice_exp(m);
 }
 
-// A' slices of M for the q-points j0..j0+nq-1 of the sum: block ql holds rows
-// 2a (P_a) and 2a+1 (Q_a) over Kp columns: the gathered columns perm_q[c],
-// c < r_q, zero beyond.
+// A' slices of M for the sum positions j0..j0+nq-1 (M^q stored by position,
+// q = qmap[j]): block ql holds rows 2a (P_a) and 2a+1 (Q_a) over Kp columns:
+// the gathered columns perm_q[c], c < r_q, zero beyond.
 __global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, const int* __restrict__ qmap,
                               const int* __restrict__ perm, const int* __restrict__ rank, int64_t n2, int j0, int nq,
                               int Kp, const int* __restrict__ row_exp, __half* __restrict__ S1,
@@ -760,7 +750,7 @@ __global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, 
     const int64_t a = rem / half, c = rem % half;
     const int q = qmap[j0 + ql];
     float2 v = make_float2(0.f, 0.f);
-    if (c < rank[q]) v = M[(int64_t)q * sq + a * np + perm[(int64_t)q * np + c]];
+    if (c < rank[q]) v = M[(int64_t)(j0 + ql) * sq + a * np + perm[(int64_t)q * np + c]];
     const int ex = row_exp[a];
     const float pr = ldexpf(v.x, ex), pi = ldexpf(v.y, ex);
     const float vals[4] = {pr, pi, pi, -pr};
@@ -820,37 +810,6 @@ __global__ void lslice_kernel(const double2* __restrict__ L, const double* __res
   }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
-// 2-D fp16 map: rows of `inner` elements, row pitch `pitch_elems`, box (BK x box_rows), 128-byte swizzle.
-bool make_map(CUtensorMap* m, const __half* base, int64_t inner, int64_t rows, int64_t pitch_elems, int box_rows) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 inline int nblk(int64_t total) {
   int64_t nb = (total + 255) / 256;
   if (nb > 152 * 32) nb = 152 * 32;
@@ -876,10 +835,11 @@ size_t syrk_tc_split_bytes(int64_t n2, int64_t kcols) {
 // Lower-triangle tiles (ti >= tj) of the n2 x n2 E' in launch order, and their
 // index by (ti, tj).  Every CTA streams the whole K extent of its row blocks and
 // about one CTA per SM is resident, so the order decides what L2 can share:
-// tiles go in bands of kGroupA row blocks, and within a band column by column,
-// so that the ~150 CTAs of a wave read about 12 + 12 row blocks instead of ~150.
-void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_of) {
-  constexpr int64_t kGroupA = 12;
+// tiles go in bands of `band` row blocks, and within a band column by column,
+// so that the ~150 CTAs of a wave read about band + 150/band row blocks instead
+// of ~150.
+void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_of, int band) {
+  const int64_t kGroupA = band < 1 ? 1 : band;
   tiles.clear();
   const int64_t nt = (n2 + tc::BM - 1) / tc::BM;
   tile_of.assign(nt * nt, -1);
@@ -895,41 +855,49 @@ void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_
 size_t syrk_tc_ws_bytes(int64_t ntiles) { return (size_t)ntiles * tc::BN * tc::BM * 2 * sizeof(float); }
 
 cudaError_t syrk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                             int nS, const int2* orb, int nf, int* row_exp) {
+                             int nS, int64_t n2, int* row_exp) {
   tc::BView bv{B, sQ, sA, nJ, qmap};
-  const int no = nf * (nf + 1) / 2;
-  tc::rrow_scale_kernel<<<no, 256, 0, st>>>(bv, orb, nf, (int64_t)nS * nJ, row_exp);
+  tc::rrow_scale_kernel<<<(unsigned)n2, 256, 0, st>>>(bv, (int64_t)nS * nJ, row_exp);
   count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
-                          const int2* orb, int nf, int j0, int nq, const int* row_exp, void* split,
-                          const int2* tiles_d, int ntiles, void* ws, int accumulate, int* err) {
+namespace {
+template <int BKt, int NST>
+cudaError_t syrk_launch(cudaStream_t st, __half* const sl[3], int64_t n2, int64_t K2, const int2* tiles_d,
+                        int ntiles, void* ws, int accumulate, int* err) {
   using namespace tc;
-  const int64_t n2 = (int64_t)nf * nf;
+  CUtensorMap m[3];
+  for (int i = 0; i < 3; ++i)
+    if (!make_map(&m[i], sl[i], K2, n2, K2, BM, BKt)) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)NST * NSLICE * (BM + BN) * BKt * 2 + 1024 + 256;
+  cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel<BKt, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  float* wh = reinterpret_cast<float*>(ws);
+  float* wl = wh + (size_t)ntiles * BN * BM;
+  TileArgs args{tiles_d, wh, wl, (int)(K2 / BKt), accumulate, err};
+  syrk_tc_kernel<BKt, NST><<<ntiles, NTHREADS, smem, st>>>(m[0], m[1], m[2], m[0], m[1], m[2], args);
+  count_launch();
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                          int64_t n2, int j0, int nq, const int* row_exp, void* split, const int2* tiles_d, int ntiles,
+                          void* ws, int accumulate, int* err, int cfg) {
+  using namespace tc;
   if (n2 <= 0 || nq <= 0 || ntiles <= 0) return cudaSuccess;
   const int64_t K2 = round_up(2 * (int64_t)nq * nJ, BK);
   __half* S1 = reinterpret_cast<__half*>(split);
   __half* S2 = S1 + (size_t)n2 * K2;
   __half* S3 = S2 + (size_t)n2 * K2;
   BView bv{B, sQ, sA, nJ, qmap};
-  const int no = nf * (nf + 1) / 2;
-  rsplit_kernel<<<nblk((int64_t)no * (K2 / 2)), 256, 0, st>>>(bv, orb, nf, j0, nq, K2, row_exp, S1, S2, S3);
+  rsplit_kernel<<<nblk(n2 * (K2 / 2)), 256, 0, st>>>(bv, n2, j0, nq, K2, row_exp, S1, S2, S3);
   count_launch();
-  CUtensorMap m[3];
-  __half* sl[3] = {S1, S2, S3};
-  for (int i = 0; i < 3; ++i)
-    if (!make_map(&m[i], sl[i], K2, n2, K2, BM)) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-  cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  float* wh = reinterpret_cast<float*>(ws);
-  float* wl = wh + (size_t)ntiles * BN * BM;
-  TileArgs args{tiles_d, wh, wl, (int)(K2 / BK), accumulate, err};
-  syrk_tc_kernel<<<ntiles, NTHREADS, smem, st>>>(m[0], m[1], m[2], m[0], m[1], m[2], args);
-  count_launch();
-  return cudaGetLastError();
+  __half* const sl[3] = {S1, S2, S3};
+  return cfg == 1 ? syrk_launch<32, 4>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err)
+                  : syrk_launch<64, 2>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err);
 }
 
 cudaError_t syrk_tc_finish(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb, int nf,
@@ -940,6 +908,26 @@ cudaError_t syrk_tc_finish(cudaStream_t st, const void* ws, int ntiles, const in
   const int64_t n2 = (int64_t)nf * nf, nt = (n2 + BM - 1) / BM, no = (int64_t)nf * (nf + 1) / 2;
   syrk_finish_kernel<<<nblk(no * no), 256, 0, st>>>(wh, wl, tile_of_d, (int)nt, orb, nf, row_exp, scale, E);
   count_launch();
+  return cudaGetLastError();
+}
+
+constexpr int kEriBlocks = 152 * 16;  // fixed grid of the fused finish (reproducible traces)
+size_t syrk_tc_eri_part_count() { return 2 * (size_t)kEriBlocks; }
+
+cudaError_t syrk_tc_finish_eri(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb,
+                               int nf, const int* row_exp, double scale, float2* eri, const double2* gamma,
+                               double2* part, double* out4) {
+  using namespace tc;
+  if (!eri && !gamma) return cudaSuccess;
+  const float* wh = reinterpret_cast<const float*>(ws);
+  const float* wl = wh + (size_t)ntiles * BN * BM;
+  const int64_t n2 = (int64_t)nf * nf, nt = (n2 + BM - 1) / BM;
+  syrk_eri_kernel<<<kEriBlocks, 256, 0, st>>>(wh, wl, tile_of_d, (int)nt, orb, nf, row_exp, scale, eri, gamma, part);
+  count_launch();
+  if (gamma) {
+    eri_traces_final_kernel<<<1, 256, 0, st>>>(part, kEriBlocks, out4);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 

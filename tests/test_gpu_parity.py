@@ -500,3 +500,108 @@ def test_exchange_matches_oracle(cuda, lib_built, c1, aniso, case, tau):
     _, _, V = o.fit(tau)
     Ko = O.exchange_matrix(o.X, V, P, cell.kmesh)
     assert np.abs(K.cpu().numpy() - Ko).max() < FP64_TOL
+
+
+# ------------------------------------------------- grouped small fragments
+def test_grouped_fragments_match_one_at_a_time(cuda, lib_built, c2):
+    """Small fragments are contracted in groups (stacked rows, block-diagonal
+    tiles).  The results equal those of each fragment contracted alone, and the
+    oracle within the mixed tolerance; the tile-order autotuner changes only the
+    order of the tiles."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, o = c2
+    frags = [W.make_fragment(wl.cell, wl.seed, i, n) for i, n in enumerate([5, 9, 14, 7, 11])]
+    g = B.Isdf(wl.cell, B.ISDF_MIXED)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(1e-7)
+    g.coulomb_metric()
+    eris, ej, ek = gpu_eri(torch, g, frags, 1)
+    for i, f in enumerate(frags):
+        e1, j1, k1 = gpu_eri(torch, g, [f], 1)
+        assert np.abs(e1[0] - eris[i]).max() < 1e-10
+        assert abs(j1[0] - ej[i]) < 1e-10 and abs(k1[0] - ek[i]) < 1e-10
+    for i in (0, 2):
+        ref, (rj, rk) = o.eri(1e-7, frags[i])
+        assert np.abs(eris[i] - ref).max() < MIXED_TOL
+        assert abs(ej[i] - rj) < MIXED_TOL and abs(ek[i] - rk) < MIXED_TOL
+    g.set_autotune(False)
+    eris2, ej2, ek2 = gpu_eri(torch, g, frags, 1)
+    for i in range(len(frags)):
+        assert np.abs(eris2[i] - eris[i]).max() < 1e-10
+    assert isinstance(g.autotune_report(), list)
+    g.close()
+
+
+def test_autotuned_tile_order_on_a_large_fragment(cuda, lib_built, c2):
+    """A fragment with several waves of tiles triggers the tile-order tuning; the
+    report names the chosen band, and the ERIs equal those without tuning."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, o = c2
+    f = W.make_fragment(wl.cell, wl.seed, 3, 40)   # n2 = 1600: 13 x 14 / 2 = 91 tiles per block
+    big = W.make_fragment(wl.cell, wl.seed, 4, 72)  # n2 = 5184: 41 x 42 / 2 = 861 tiles
+    res = []
+    for tune in (True, False):
+        g = B.Isdf(wl.cell, B.ISDF_MIXED)
+        g.set_autotune(tune)
+        g.build_points(wl.n_p, wl.seed)
+        g.fit_zeta(1e-7)
+        g.coulomb_metric()
+        res.append(gpu_eri(torch, g, [f, big], 1))
+        rep = g.autotune_report()
+        if tune:
+            assert any(e["tiles"] >= 861 and e["band"] in (6, 12, 24) for e in rep), rep
+        else:
+            assert rep == []
+        g.close()
+    for i in range(2):
+        assert np.abs(res[0][0][i] - res[1][0][i]).max() < 1e-10
+        assert abs(res[0][1][i] - res[1][1][i]) < 1e-10
+
+
+@pytest.mark.parametrize("pipeline,band", [(0, 12), (1, 12), (1, 5)])
+def test_tile_schedules_match_oracle(cuda, lib_built, c2, pipeline, band):
+    """Each pipeline of the tensor-core tile kernel (K rows of 64 fp16 in 2
+    stages, rows of 32 fp16 in 4 stages) and tile order gives the oracle's ERIs."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, o = c2
+    f = W.make_fragment(wl.cell, wl.seed, 4, 40)
+    g = B.Isdf(wl.cell, B.ISDF_MIXED)
+    g.set_tile_schedule(pipeline, band)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(1e-7)
+    g.coulomb_metric()
+    eris, ej, ek = gpu_eri(torch, g, [f], 1)
+    ref, (rj, rk) = o.eri(1e-7, f)
+    assert np.abs(eris[0] - ref).max() < MIXED_TOL
+    assert abs(ej[0] - rj) < MIXED_TOL and abs(ek[0] - rk) < MIXED_TOL
+    with pytest.raises(B.IsdfError):
+        g.set_tile_schedule(2, 12)
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["c1", "c2"])
+def test_emulated_fit_gemm_matches_fp64(cuda, lib_built, c1, c2, case):
+    """In the mixed path g^k = conj(X^k) Phi^k (Eq. 5) runs on the tensor cores with
+    seven exact 7-bit slices per operand; eta^q then equals the FP64 path's to
+    ~1e-14 relative, and the ranks of the factor of Pi^q are the same."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, o = c1 if case == "c1" else c2
+    s = {}
+    for prec in (B.ISDF_FP64, B.ISDF_MIXED):
+        g = B.Isdf(wl.cell, prec)
+        g.build_points(wl.n_p, wl.seed)
+        ranks = g.fit_zeta(1e-7)
+        sz = g.sizes()
+        eta = torch.empty((sz["nk"], sz["np"], sz["ng"]), dtype=torch.complex128, device="cuda")
+        g.get(2, eta)
+        s[prec] = (eta.cpu().numpy(), ranks)
+        g.close()
+    e64, em = s[B.ISDF_FP64][0], s[B.ISDF_MIXED][0]
+    assert np.abs(em - e64).max() < 1e-12 * np.abs(e64).max()
+    assert np.array_equal(s[B.ISDF_FP64][1], s[B.ISDF_MIXED][1])
+    ref = o.eta
+    assert np.abs(em - ref).max() < 1e-12 * np.abs(ref).max()
