@@ -5,7 +5,7 @@ and interpolation points, the fit of zeta^q, the Coulomb metric V^q and the
 ERIs of every fragment (written to device buffers) with their J/K traces.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c5]
-                  [--precision mixed|fp64] [--impl gb300|reference]
+                  [--precision mixed|fp64|fp64tc] [--impl gb300|reference]
 
 The default workload is c5 (Nk = 10^3, 24^3 grid, N_P = 300, 64 fragments
 with n_f ~ U[40, 200]), the configuration the headline metric is quoted on;
@@ -109,22 +109,44 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- profile lookup
-def profile_traffic(kernel_file: str, workload: str):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
-    or None.  A summary counts only if it records the same workload string
-    (overrides included) and the hash of the kernel source it was taken on."""
-    src = ROOT / "paper_2601_16379_gb300" / "csrc" / kernel_file
-    if not src.exists():
+# Source regions of the dominant kernels: a committed ncu summary applies only
+# while the kernel's own source is the one it was taken on.
+KERNEL_REGIONS = {
+    "syrk_tc_kernel<64, 2>": ("k_tc.cu", "template <int BKt, int NST>\n__global__ void __launch_bounds__(NTHREADS, 1)\n"
+                              "    syrk_tc_kernel(", "// ----------------------------------------------------------------- helpers"),
+    "syrk4_tc_kernel": ("k_tc64.cu", "__global__ void __launch_bounds__(NT4, 1)\n    syrk4_tc_kernel(",
+                        "// B viewed as element"),
+}
+
+
+def kernel_source_hash(kernel: str):
+    f, start, end = KERNEL_REGIONS[kernel]
+    src = (ROOT / "paper_2601_16379_gb300" / "csrc" / f).read_text()
+    i = src.find(start)
+    j = src.find(end, i + 1)
+    if i < 0 or j < 0:
         return None
-    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    return hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, flops_per_launch: float):
+    """DRAM bytes per launch of the dominant kernel, or None: the DRAM bytes per
+    algorithmic flop of a committed small-case ncu capture of the same kernel
+    source (profiles/*.md: 'kernel:', 'kernel_source_sha256_16:',
+    'traffic_bytes_per_algorithmic_flop:') times this launch's algorithmic flops.
+    The scaling assumes traffic in proportion to the work of a launch (the same
+    tile order and tile size, so the same reuse per tile-k-step)."""
+    h = kernel_source_hash(kernel)
+    if h is None:
+        return None, None
     for prof in sorted((ROOT / "profiles").glob("*.md")):
         text = prof.read_text()
-        m = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
-        w = re.search(r"^workload:\s*(.+)$", text, re.M)
-        t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-        if m and w and t and m.group(1) == h and w.group(1).strip() == workload.strip():
-            return float(t.group(1))
-    return None
+        k = re.search(r"^kernel:\s*(.+)$", text, re.M)
+        m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+        t = re.search(r"traffic_bytes_per_algorithmic_flop:\s*([0-9.eE+-]+)", text)
+        if k and m and t and k.group(1).strip() == kernel and m.group(1) == h:
+            return float(t.group(1)) * flops_per_launch, prof.name
+    return None, None
 
 
 def reduce_max_over_ranks(values, dist, device):
@@ -170,7 +192,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    prec = B.ISDF_MIXED if args.precision == "mixed" else B.ISDF_FP64
+    prec = {"mixed": B.ISDF_MIXED, "fp64": B.ISDF_FP64, "fp64tc": B.ISDF_FP64_TC}[args.precision]
     wl = W.workload(args.workload, kmesh=args.kmesh, mesh=args.mesh, frag_sizes=_frag_sizes(args))
     # fragment partition: every rank builds X and V^q, contracts its share of the
     # fragments, and the traces are gathered (one sum-reduction per step)
@@ -253,7 +275,14 @@ def run_gpu(args, rank, world, local_rank):
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(done)]
     ms = evs[0].elapsed_time(evs[-1]) / done
     launches = (g.launch_count() - launches0) // done
-    herk_ms, herk_n, herk_flops = g.stage_time(5)
+    # the dominant kernel on its own: stage 6 holds one CUDA-event record per launch of the
+    # tensor-core E' kernel (mixed path); the FP64 path has only the stage as a whole
+    herk_ms, herk_n, herk_flops = g.stage_time(6)
+    kernel_name = ("syrk4_tc_kernel" if prec == B.ISDF_FP64_TC else "syrk_tc_kernel") + \
+        ": E' = c sum_q R^q R^qT on tcgen05 (stage 5 without slicing and finish)"
+    if herk_n == 0:
+        herk_ms, herk_n, herk_flops = g.stage_time(5)
+        kernel_name = "fragment E = sum_q B^q B^q^H (stage 5)"
     stage = {name: g.stage_time(i) for i, name in enumerate(["points", "fit", "coulomb", "pair_tensor", "B=ML", "E=BB^H"])}
     g.timing(False)
     clk = clocks.stop()
@@ -284,7 +313,7 @@ def run_gpu(args, rank, world, local_rank):
     ms, e2e_ms = reduce_max_over_ranks([ms, e2e_ms], dist, "cuda")
 
     peaks, peak_src = measured_peaks()
-    if prec == B.ISDF_MIXED:
+    if prec != B.ISDF_FP64:
         # tcgen05 kind::f16 (fp16 operands); fp16 and bf16 have the same nominal dense rate,
         # and the kernel runs inside a long step, so the sustained bf16 measurement applies
         bound = "tensor"
@@ -293,6 +322,13 @@ def run_gpu(args, rank, world, local_rank):
     else:
         bound, peak, peak_name = "alu", 1.20, "FP64 FMA measured on this GB300 (1.20 TFLOP/s)"
     herk_avg_ms = herk_ms / max(herk_n, 1)
+    traffic, traffic_src = None, None
+    if herk_n and kernel_name.startswith("syrk"):
+        kname = "syrk4_tc_kernel" if prec == B.ISDF_FP64_TC else "syrk_tc_kernel<64, 2>"
+        traffic, prof = profile_traffic(kname, herk_flops / herk_n)
+        if traffic is not None:
+            traffic_src = (f"{prof}: DRAM bytes per algorithmic flop of a small-case capture of {kname}, "
+                           f"times this launch's algorithmic flops")
     achieved = (herk_flops / max(herk_n, 1)) / (herk_avg_ms * 1e-3) / 1e12 if herk_n else None
     workload_name = f"{args.workload}: {wl.description}" + _overrides(args)
     r = ranks_q.get("r")
@@ -311,7 +347,9 @@ def run_gpu(args, rank, world, local_rank):
         "higher_is_better": False,
         "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None,
-        "dtype": "f64 fit + f32/fp16-slice fragment contraction" if prec == B.ISDF_MIXED else "f64",
+        "dtype": {B.ISDF_MIXED: "f64 fit + f32/fp16-slice fragment contraction",
+                  B.ISDF_FP64_TC: "f64 fit + float-float/exact fp16-slice (5, 4 slices) fragment contraction",
+                  B.ISDF_FP64: "f64"}[prec],
         "data": "synthetic (seeded cell, Gaussian basis and fragment orbitals)",
         "config": {"workload": workload_name, "precision": args.precision,
                    "solve_tol": args.solve_tol, "fragments": len(frags),
@@ -324,12 +362,12 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "eri_out": "page-locked host buffer of the largest fragment, reused"},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "fragment E = sum_q B^q B^q^H (stage 5)", "bound": bound, "achieved": achieved,
+        "roofline": {"kernel": kernel_name, "bound": bound, "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "peak_source": peak_name,
                      "algorithmic_flops_per_launch": herk_flops / max(herk_n, 1),
                      "avg_launch_ms": herk_avg_ms, "launches": herk_n,
-                     "traffic": profile_traffic("k_tc.cu", workload_name)},
+                     "traffic": traffic, "traffic_source": traffic_src},
         "stages_ms_per_step": {k: v[0] / done for k, v in stage.items()},
         "clocks": clk,
         "traces_fragment0": {"E_J": float(ej[0]), "E_K": float(ek[0])},
@@ -347,12 +385,16 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.empty_cache()
 
     if rank == 0 and prec == B.ISDF_MIXED and not args.no_accuracy:
-        est = accuracy_cost_s(wl, fit_s)
+        est = accuracy_cost_s(wl, fit_s, ms / 1e3)
         if budget.left() > est + CPU_BASELINE_S:
             release()
-            result["accuracy"] = accuracy_vs_fp64(wl, args.solve_tol)
+            result["accuracy"] = accuracy_vs_fp64(wl, args.solve_tol, np.asarray(ej), np.asarray(ek))
         else:
             result["accuracy"] = {"skipped": f"wall-clock budget ({budget.left():.0f} s left, ~{est:.0f} s needed)"}
+    if rank == 0 and not args.no_next and budget.left() > 60.0 + CPU_BASELINE_S:
+        # the paper's further uses of the same X and V^q, on a handle of their own
+        release()
+        result["next_rows"] = next_rows(wl, prec, args.solve_tol)
     if rank == 0 and args.nk_scan and args.workload == "c5" and not (args.kmesh or args.mesh or args.frag_sizes):
         # linear cost in Nk (Section IV): the same fragment set on smaller k-meshes
         release()
@@ -365,6 +407,54 @@ def run_gpu(args, rank, world, local_rank):
         print(json.dumps(result))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def next_rows(wl, prec, solve_tol):
+    """Device time (CUDA events, one warm-up call first) of the k-point exchange
+    matrix (Eq. 10) and of the k-SOS-MP2 polarisability chi^Q(tau) with its
+    opposite-spin trace (Eqs. 11-15) on the workload's X^k and V^q (a handle of
+    their own: points, fit, Coulomb metric), with seeded stand-ins for the
+    density matrices, orbitals and orbital energies."""
+    import torch
+    from paper_2601_16379_gb300 import binding as B
+    from paper_2601_16379_gb300 import workloads as W
+
+    g = B.Isdf(wl.cell, prec)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(solve_tol)
+    g.coulomb_metric()
+
+    cell = wl.cell
+    nk, nao, npp = cell.nkpts, cell.nao, wl.n_p
+    rng = np.random.default_rng(11)
+    Cs = rng.standard_normal((nk, nao, 4)) + 1j * rng.standard_normal((nk, nao, 4))
+    P = torch.from_numpy(np.einsum("kmi,kni->kmn", Cs, Cs.conj()) / nao).cuda()
+    K = torch.empty_like(P)
+    n_occ = max(1, nao // 4)
+    C = torch.from_numpy(W.mo_coefficients(cell, 17)).cuda()
+    eps = W.orbital_energies(cell, 17, n_occ)
+    chi = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    t_x = timed(lambda: g.exchange(P, K))
+    t_s = timed(lambda: g.sos_polarizability(C, eps, n_occ, 0.6, chi))
+    out = {"exchange_eq10": {"s": round(t_x, 4), "what": f"K^k for all {nk} k, N_AO = {nao}, N_P = {npp} (FP64)"},
+           "sos_mp2_eq11_15": {"s": round(t_s, 4),
+                               "what": f"chi^Q(tau) for all {nk} Q and S(tau), one tau, {n_occ} occupied of "
+                                       f"{nao} orbitals per k, N_P = {npp} (FP64)"}}
+    del P, K, C, chi
+    g.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def nk_scan(args, prec, budget, meshes=(2, 4, 6, 8)):
@@ -442,24 +532,29 @@ def _paired_q_count(kmesh):
     return cnt
 
 
-def accuracy_cost_s(wl, fit_s):
+def accuracy_cost_s(wl, fit_s, step_s):
     """Rough wall time of accuracy_vs_fp64: the points, fit and Coulomb metric in
-    both precisions (the FP64 Coulomb GEMM is slower) plus the FP64 contraction of
-    the sampled fragments at ~1 TFLOP/s."""
+    three precisions (the FP64 Coulomb GEMM is slower), the FP64_TC build of every
+    fragment (~2.5 mixed steps), and the FP64 contraction of the sampled fragments
+    at ~1 TFLOP/s."""
     nsum = _paired_q_count(wl.cell.kmesh)
     sizes = [f.norb for f in wl.fragments]
     fl = [4.0 * (s * s) ** 2 * nsum * wl.n_p for s in sizes]
     ok = [x for x in fl if x <= FP64_FLOP_BUDGET]
-    return 4.0 * fit_s + (max(ok) if ok else 0.0) / 1.0e12 + min(fl) / 1.0e12 + 30.0
+    return 6.0 * fit_s + 2.5 * step_s + (max(ok) if ok else 0.0) / 1.0e12 + min(fl) / 1.0e12 + 30.0
 
 
-def accuracy_vs_fp64(wl, solve_tol):
-    """Max-abs ERI error and |dE_J|, |dE_K| (Ha) of the mixed path against the
-    FP64 path on the same GPU, for the smallest fragment and the largest one
-    whose FP64 contraction fits FP64_FLOP_BUDGET.  The FP64 path is timed on
-    the way (CUDA events): points + fit + Coulomb metric, and each sampled
-    fragment on its own, from which its whole build is extrapolated with
-    t(n_f) = a n_f^4 + b n_f^2 (the E and pair/B terms) fitted to the two."""
+def accuracy_vs_fp64(wl, solve_tol, ej_mixed, ek_mixed):
+    """Accuracy of the mixed path (Ha) against two FP64-class references on the
+    same GPU, with their cost:
+      * FP64_TC (float-float pair tensor, exact-slice tensor-core contractions):
+        the whole workload, timed with CUDA events (points + fit + Coulomb metric,
+        then every fragment); its traces are compared with the mixed step's for
+        every fragment, its ERIs on the sampled fragments;
+      * FP64 (FP64 arithmetic throughout): the smallest fragment and the largest
+        whose contraction fits FP64_FLOP_BUDGET, each timed on its own; the whole
+        FP64 build is extrapolated with t(n_f) = a n_f^4 + b n_f^2 fitted to them.
+    The mixed ERIs of the sampled fragments come from a fresh mixed handle."""
     import torch
     from paper_2601_16379_gb300 import binding as B
 
@@ -477,6 +572,27 @@ def accuracy_vs_fp64(wl, solve_tol):
         e = torch.cuda.Event(enable_timing=True)
         e.record()
         return e
+
+    # FP64_TC over the whole workload; ERIs kept for the sampled fragments only
+    g = B.Isdf(cell, B.ISDF_FP64_TC)
+    Cs = [torch.from_numpy(f.C).cuda() for f in wl.fragments]
+    gs = [torch.from_numpy(f.gamma).cuda() for f in wl.fragments]
+    outs = [torch.empty((f.norb,) * 4, dtype=torch.complex128, device="cuda") if i in pick else None
+            for i, f in enumerate(wl.fragments)]
+    torch.cuda.synchronize()
+    e0 = ev()
+    g.build_points(np_, wl.seed)
+    g.fit_zeta(solve_tol)
+    g.coulomb_metric()
+    e1 = ev()
+    ej_tc, ek_tc = g.fragment_eri(Cs, gs, outs)
+    e2 = ev()
+    torch.cuda.synchronize()
+    tc_fit, tc_frag = e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3
+    res["tc"] = ([outs[i].cpu().numpy() for i in pick], [ej_tc[i] for i in pick], [ek_tc[i] for i in pick])
+    del outs, Cs, gs
+    g.close()
+    torch.cuda.empty_cache()
 
     for prec in (B.ISDF_FP64, B.ISDF_MIXED):
         g = B.Isdf(cell, prec)
@@ -504,17 +620,28 @@ def accuracy_vs_fp64(wl, solve_tol):
         del outs, Cs, gs
         g.close()
         torch.cuda.empty_cache()
-    d, m = res[B.ISDF_FP64], res[B.ISDF_MIXED]
+    d, m, t = res[B.ISDF_FP64], res[B.ISDF_MIXED], res["tc"]
     per = []
     for i, f in enumerate(frags):
-        per.append({"n_f": f.norb, "max_abs_eri": float(np.abs(m[0][i] - d[0][i]).max()),
+        per.append({"n_f": f.norb,
+                    "max_abs_eri": float(np.abs(m[0][i] - d[0][i]).max()),
                     "dE_J": float(abs(m[1][i] - d[1][i])), "dE_K": float(abs(m[2][i] - d[2][i])),
+                    "fp64tc_max_abs_eri": float(np.abs(t[0][i] - d[0][i]).max()),
+                    "fp64tc_dE_J": float(abs(t[1][i] - d[1][i])), "fp64tc_dE_K": float(abs(t[2][i] - d[2][i])),
                     "E_J": float(d[1][i]), "E_K": float(d[2][i]),
                     "fp64_s": round(timing[B.ISDF_FP64][1][i], 4), "mixed_s": round(timing[B.ISDF_MIXED][1][i], 4)})
-    worst = max(max(x["max_abs_eri"], x["dE_J"], x["dE_K"]) for x in per)
-    out = {"reference": "FP64 path on the same GPU (pinned to the FP64 oracle by the parity tests)",
+    dj = np.abs(np.asarray(ej_mixed) - np.asarray(ej_tc))
+    dk = np.abs(np.asarray(ek_mixed) - np.asarray(ek_tc))
+    worst = max(max(max(x["max_abs_eri"], x["dE_J"], x["dE_K"]) for x in per), float(dj.max()), float(dk.max()))
+    out = {"reference": "FP64_TC path, every fragment (traces) and the sampled fragments (ERIs); FP64 path on "
+                        "the sampled fragments (same GPU; both pinned to the FP64 oracle by the parity tests)",
            "unit": "Ha", "tolerance": 1e-6, "max_error": worst, "within_tolerance": bool(worst <= 1e-6),
-           "fragments": per}
+           "all_fragments_vs_fp64tc": {"fragments": len(sizes), "max_dE_J": float(dj.max()),
+                                       "max_dE_K": float(dk.max())},
+           "fragments": per,
+           "fp64tc_path": {"build_s": round(tc_fit + tc_frag, 3), "points_fit_coulomb_s": round(tc_fit, 3),
+                           "fragments_s": round(tc_frag, 3),
+                           "note": "measured (CUDA events), the whole workload in one call"}}
     fit64, tf = timing[B.ISDF_FP64]
     ns = [f.norb for f in frags]
     if len(ns) == 2 and ns[0] != ns[1]:
@@ -650,7 +777,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c5")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64tc"])
     ap.add_argument("--solve-tol", type=float, default=SOLVE_TOL)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--budget-s", type=float, default=1200.0,
@@ -660,6 +787,7 @@ def main():
                     help="seconds kept after the timed steps for the accuracy check and the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed vs FP64 comparison")
+    ap.add_argument("--no-next", action="store_true", help="skip the exchange / SOS-MP2 timings")
     ap.add_argument("--nk-scan", type=int, default=1, help="1: time the c5 fragment set on 2^3..8^3 k-meshes too")
     ap.add_argument("--kmesh", type=int, default=None, help="k-mesh side override (Nk scan)")
     ap.add_argument("--mesh", type=int, default=None, help="real-space grid side override (small profiling cases)")

@@ -60,10 +60,17 @@ typedef enum {
 
 typedef enum {
   ISDF_FP64 = 0,   /* every step in FP64                                          */
-  ISDF_MIXED = 1   /* FP64 points and fit (Eqs. 3-5) and the factors of V (Eq. 6);  */
-                   /* the grid FFT and V GEMM in complex64, the fragment pair      */
-                   /* tensor and ERI contractions (Eqs. 19-20) in reduced precision */
-                   /* (compensated FP32 SIMT; exact fp16 slices on the tensor cores) */
+  ISDF_MIXED = 1,  /* FP64-class points and fit (Eqs. 3-5); V (Eq. 6) from a float-  */
+                   /* float grid FFT and V_xi on the tensor cores with four exact   */
+                   /* fp16 slices; the fragment pair tensor and ERI contractions   */
+                   /* (Eqs. 19-20) in reduced precision (FP32 transforms, three-    */
+                   /* and four-slice exact fp16 products on the tensor cores)       */
+  ISDF_FP64_TC = 2 /* FP64-class results on the tensor cores: points and fit as in  */
+                   /* ISDF_MIXED, V in FP64; the pair tensor in float-float (~2^-44), */
+                   /* B = M L with five and E with four exact fp16 slices per       */
+                   /* operand (~2^-28 of |R_a||R_b|; Ozaki-scheme emulation); the   */
+                   /* ERIs complex128.  Falls back to FP64 arithmetic for a        */
+                   /* fragment set whose 2 max r_q exceeds 576.                    */
 } isdf_precision;
 
 /* Cell, basis and sampling (Eq. 1; Section II).
@@ -143,8 +150,8 @@ int isdf_coulomb_metric_eta(isdf_handle* h, void* V_out);
  *   C[f]       device complex128 [Nk][N_AO][n_orb[f]]
  *   gamma[f]   device complex128 [n_orb][n_orb] Hermitian density matrix with
  *              density n = sum_pq gamma_pq phi_p^* phi_q; array or entry may be NULL
- *   eri_out[f] complex128 [p][q][r][s] chemist's (pq|rs) in FP64 mode,
- *              complex64 in MIXED mode; device memory or page-locked host
+ *   eri_out[f] complex128 [p][q][r][s] chemist's (pq|rs) in FP64 and FP64_TC
+ *              mode, complex64 in MIXED mode; device memory or page-locked host
  *              memory (written by the kernel over the host link, e.g. when the
  *              ERIs of all fragments exceed HBM); array or entry may be NULL
  *   ej_out[f]  E_J = 1/2 sum gamma_pq gamma_rs (pq|rs)          (host, may be NULL)
@@ -272,6 +279,8 @@ int64_t isdf_launch_count(const isdf_handle* h);
  *   stage 0  interpolation points (S0-S1)        stage 3  fragment pair tensor M^q (S4a)
  *   stage 1  fit of zeta (S2)                    stage 4  B^q = M^q L^q (S4b, first half)
  *   stage 2  Coulomb metric (S3)                 stage 5  E = sum_q B^q B^q^H (S4b, dominant)
+ *   stage 6  the tensor-core kernel of stage 5 alone (mixed path: one record per
+ *            launch of the E' kernel, without its slicing and finish)
  * the summed device milliseconds, the number of recorded launches of that
  * stage, and its algorithmic floating-point work (flops) summed over them. */
 int isdf_timing_enable(isdf_handle* h, int enable);

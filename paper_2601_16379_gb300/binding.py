@@ -18,6 +18,7 @@ LIB_PATH = _PKG / "libisdf.so"
 
 ISDF_FP64 = 0
 ISDF_MIXED = 1
+ISDF_FP64_TC = 2
 
 STATUS = {0: "ISDF_OK", -1: "ISDF_ERR_ARG", -2: "ISDF_ERR_OOM", -3: "ISDF_ERR_CUDA",
           -4: "ISDF_ERR_NUMERIC", -5: "ISDF_ERR_TIMEOUT", -6: "ISDF_ERR_STATE"}

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include "ff.cuh"
+
 namespace isdf {
 
 // ---------------------------------------------------------------- complex ops
@@ -133,6 +135,9 @@ cudaError_t grid_coulomb_fft(cudaStream_t st, double2* x, int rows_per_q, int q0
                              const CellDev& c, const double2* dtw, void* work);
 cudaError_t grid_coulomb_fft_f(cudaStream_t st, float2* x, int rows_per_q, int q0, int nq,
                                const CellDev& c, const double2* dtw, void* work);
+// the same in float-float (FP32 arithmetic, ~2^-44), in place on float-float data
+cudaError_t grid_coulomb_fft_ff(cudaStream_t st, ffcomplex* x, int rows_per_q, int q0, int nq,
+                                const CellDev& c, const double2* dtw, void* work);
 void grid_twiddles(const int mesh[3], double2* host192);
 
 // Real k-mesh DFT out of place, keeping the q with qslot[q] >= 0 (complex64 output):
@@ -145,6 +150,18 @@ cudaError_t kdft_real_f(cudaStream_t st, const float* in, float2* out, int64_t n
 // Rows row0 .. row0 + n_f^2 - 1 of a stack of `rows` rows: Zr[R][row0 + row][I].
 cudaError_t pair_products_real_f(cudaStream_t st, const float2* t, int nk, int np, int nf, float* Zr, int64_t row0,
                                  int64_t rows);
+// Float-float variants for the FP64-class tensor-core path (ff.cuh): the k -> R
+// DFT of T, the real pair rows and their R -> q DFT, in FP32 arithmetic at ~2^-44.
+cudaError_t z2ff(cudaStream_t st, const double2* in, ffcomplex* out, int64_t n);
+cudaError_t kdft_cols_ff(cudaStream_t st, ffcomplex* data, int64_t ncol, KMesh km, int s1, int s2, int mode,
+                         double scale);
+// complex128 data transformed in float-float (as kdft_cols, ~2^-44 relative)
+cudaError_t kdft_cols_zff(cudaStream_t st, double2* data, int64_t ncol, KMesh km, int s1, int s2, int mode,
+                          double scale);
+cudaError_t kdft_real_ff(cudaStream_t st, const ffloat* in, ffcomplex* out, int64_t ncol, KMesh km, int s,
+                         double scale, const int* qslot);
+cudaError_t pair_products_real_ff(cudaStream_t st, const ffcomplex* t, int nk, int np, int nf, ffloat* Zr,
+                                  int64_t row0, int64_t rows);
 // Fragment pair products Z[R][(p q)][I] = conj(t[R][I][p]) * t[R][I][q].
 cudaError_t pair_products(cudaStream_t st, const double2* t, int nk, int np, int nf, double2* Z);
 
@@ -162,8 +179,9 @@ const char* noalloc_last_error();
 // (a, k = Q nJ + J) -> B[slot(Q) sQ + a sA + J] with slot(Q) = qmap[Q] (or Q when
 // qmap is NULL), J < nJ, over the nS positions of the sum.  Row exponents over
 // all positions, then each chunk of positions (accumulate = 0 for the first),
-// then the finish to E (complex128 n_f^2 x n_f^2, full, in the pair basis (pq))
-// times scale; orb: the orbits of pair_orbits (device copy, n_f (n_f+1)/2 entries).
+// then the finish (E = W E' W^H times scale, written as the chemist-order ERIs
+// with the traces on the way); orb: the orbits of pair_orbits (device copy,
+// n_f (n_f+1)/2 entries).
 void pair_orbits(int nf, std::vector<int2>& orb);
 size_t syrk_tc_split_bytes(int64_t n2, int64_t kcols);
 void syrk_tc_tiles(int64_t n2, std::vector<int2>& tiles, std::vector<int>& tile_of, int band = 12);
@@ -175,15 +193,55 @@ cudaError_t syrk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64
 cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
                           int64_t n2, int j0, int nq, const int* row_exp, void* split, const int2* tiles_d, int ntiles,
                           void* ws, int accumulate, int* err, int cfg = 0);
-cudaError_t syrk_tc_finish(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb, int nf,
-                           const int* row_exp, double scale, double2* E);
+// The two halves of syrk_tc_chunk: the fp16 slices of the chunk's rows, then the
+// tensor-core kernel over them (timed on its own as the dominant kernel).
+// corr (n2 doubles, or NULL) accumulates per row the products of the row with
+// itself that the contraction leaves out (added to E'_aa by the finish).
+cudaError_t syrk_tc_split(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                          int64_t n2, int j0, int nq, const int* row_exp, void* split, double* corr);
+cudaError_t syrk_tc_mma(cudaStream_t st, void* split, int64_t n2, int nq, int64_t nJ, const int2* tiles_d,
+                        int ntiles, void* ws, int accumulate, int* err, int cfg);
 // The finish fused with the chemist's permutation (eri: complex64 [p][q][r][s], or
-// NULL) and the FP64 traces (gamma, or NULL: out4 = E_J, E_K, Im E_J, Im E_K);
-// part: syrk_tc_eri_part_count() double2 of scratch.  E is never stored.
+// NULL; complex128 for the _z variant) and the FP64 traces of a Hermitian gamma
+// (or NULL: out4 = E_J, E_K, 0, 0); part: syrk_tc_eri_part_count() double2 of
+// scratch.  E is never stored.
 size_t syrk_tc_eri_part_count();
 cudaError_t syrk_tc_finish_eri(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb,
-                               int nf, const int* row_exp, double scale, float2* eri, const double2* gamma,
-                               double2* part, double* out4);
+                               int nf, const int* row_exp, const double* corr, double scale, float2* eri,
+                               const double2* gamma, double2* part, double* out4);
+cudaError_t syrk_tc_finish_eri_z(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb,
+                                 int nf, const int* row_exp, const double* corr, double scale, double2* eri,
+                                 const double2* gamma, double2* part, double* out4);
+
+// ---- FP64-class tensor-core contractions (k_tc64.cu): E' with four exact fp16
+// slices of the float-float rows of B, B = M L with five exact slices of the
+// float-float M and of L.  Same workspace, tile lists and finish as above.
+size_t syrk4_tc_split_bytes(int64_t n2, int64_t kcols);
+cudaError_t syrk4_tc_rowscale(cudaStream_t st, const ffcomplex* B, int64_t sQ, int64_t sA, int64_t nJ, int nS,
+                              int64_t n2, int* row_exp);
+cudaError_t syrk4_tc_split(cudaStream_t st, const ffcomplex* B, int64_t sQ, int64_t sA, int64_t nJ, int64_t n2,
+                           int j0, int nq, const int* row_exp, void* split, double* corr);
+cudaError_t syrk4_tc_mma(cudaStream_t st, void* split, int64_t n2, int nq, int64_t nJ, const int2* tiles_d,
+                         int ntiles, void* ws, int accumulate, int* err);
+int mlgemm5_tc_kp(int rp);
+bool mlgemm5_tc_supported(int rp);
+size_t mlgemm5_tc_lslice_bytes(int nk, int rp, int nj);
+size_t mlgemm5_tc_split_bytes(int64_t n2, int rp, int nq);
+cudaError_t mlgemm5_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, const int* perm,
+                               const int* rank, int rp, int nj, void* lsl, int* col_exp);
+cudaError_t mlgemm5_tc_rowscale(cudaStream_t st, const ffcomplex* M, int64_t sq, int np, const int* qmap, int nS,
+                                const int* perm, const int* rank, int rp, int64_t n2, int* row_exp);
+cudaError_t mlgemm5_tc_chunk(cudaStream_t st, ffcomplex* M, int64_t sq, const int* qmap, int64_t n2, int np,
+                             const int* perm, const int* rank, int rp, int nj, int j0, int nq, const int* row_exp,
+                             void* split, const void* lsl, const int* col_exp, int nk, int* err);
+// V_xi^q = Omega conj(c'^q) c'^q^T (Eq. 6) on the tensor cores, FP64-class: c' rows
+// [q][I < rx][G < ng] float-float (q stride qs), V[q][I][J] complex128 (row pitch ldv,
+// q stride vs).  work: vxi_tc_work_bytes(rx, ng, qc) bytes for chunks of qc q-points
+// (vxi_tc_chunk picks qc for a byte budget); err: bounded-wait error word.
+int vxi_tc_chunk(int rx, int ng, size_t budget);
+size_t vxi_tc_work_bytes(int rx, int ng, int qc);
+cudaError_t vxi_tc(cudaStream_t st, const ffcomplex* c, int64_t qs, int rx, int ng, int nq, double omega,
+                   double2* V, int64_t ldv, int64_t vs, void* work, int qc, int* err);
 // B^q = M^q L^q (w_q^{1/2} folded into L) on the tensor cores with four exact
 // integer slices, over the structural nonzeros of L^q only: the rp = max_q r_q
 // pivot columns perm_q[c] (c < rank_q) of M^q and the nj output columns.  M^q is

@@ -85,7 +85,7 @@ struct isdf_handle {
   };
   std::vector<TuneEntry> tune_log;
   // per-stage event timing
-  static constexpr int kStages = 6;
+  static constexpr int kStages = 7;
   bool timing = false;
   double stage_ms[kStages] = {0};
   int64_t stage_n[kStages] = {0};
@@ -167,7 +167,7 @@ struct isdf_handle {
   // them, or isdf_coulomb_metric_eta, then needs a new isdf_fit_zeta).
   static bool in_frag_group(const std::string& n) { return n.rfind("frag_", 0) == 0 || n.rfind("tc_", 0) == 0; }
   static bool in_fit_group(const std::string& n) {
-    return n == "eta" || n == "xi" || n == "xi_f" || n == "grid_work" || n == "grid_work_emu";
+    return n == "eta" || n == "xi" || n == "grid_work" || n == "grid_work_emu" || n == "grid_work_v";
   }
   bool evict_other(const char* name) {
     const std::string n(name);
@@ -390,10 +390,10 @@ int finish_points(isdf_handle* h) {
 // smaller ones are stacked (ascending size) while the group's scratch -- pair
 // rows Z and M^q per row (padded to a tile boundary), and E per fragment -- stays
 // within what the largest fragment of the call needs alone (or kMinBytes).
-std::vector<std::vector<int>> fragment_groups(int n, const int32_t* n_orb, int nk, int nS, int np) {
+std::vector<std::vector<int>> fragment_groups(int n, const int32_t* n_orb, int nk, int nS, int np, double esz) {
   constexpr int64_t kWaves = 4, kSMs = 152;
   constexpr double kMinBytes = 4.0 * (1 << 30);
-  const double per_row = (double)np * (4.0 * nk + 8.0 * nS);
+  const double per_row = esz * (double)np * (4.0 * nk + 8.0 * nS);
   auto n2of = [&](int f) { return (int64_t)n_orb[f] * n_orb[f]; };
   int64_t n2max = 0;
   for (int f = 0; f < n; ++f) n2max = std::max(n2max, n2of(f));
@@ -514,7 +514,7 @@ int isdf_create(const isdf_cell_desc* c, isdf_precision precision, void* cuda_st
   if (!out) return ISDF_ERR_ARG;
   *out = nullptr;
   if (!c) return ISDF_ERR_ARG;
-  if (precision != ISDF_FP64 && precision != ISDF_MIXED) return ISDF_ERR_ARG;
+  if (precision != ISDF_FP64 && precision != ISDF_MIXED && precision != ISDF_FP64_TC) return ISDF_ERR_ARG;
   if (c->natm < 1 || c->nshell < 1 || !c->coords || !c->shell_atom || !c->shell_l || !c->shell_nprim ||
       !c->exps || !c->coefs)
     return ISDF_ERR_ARG;
@@ -709,10 +709,11 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
            np, (int64_t)np * np, nk));
   CK(kdft_cols(h->st, Pi, (int64_t)np * np, km, +1, -1, 1, 1.0 / nk));
   // eta^q (Eq. 5): g^k_I(r) = sum_mu conj(X^k_I mu) Phi^k_mu(r), then the k-convolution.
-  // In the mixed path g runs on the tensor cores with seven exact slices per
-  // operand (~2^-48 relative, FP64-class); the FP64 path keeps FP64 arithmetic.
+  // In the mixed and FP64_TC paths g runs on the tensor cores with seven exact
+  // slices per operand (~2^-48 relative, FP64-class); the FP64 path keeps FP64
+  // arithmetic.
   ENSURE(eta, double2, "eta", (size_t)nk * np * ng);
-  if (h->prec == ISDF_MIXED && zgemm_emu_supported(nao)) {
+  if (h->prec != ISDF_FP64 && zgemm_emu_supported(nao)) {
     const size_t per_k = zgemm_emu_work_bytes(np, ng, nao, 1);
     const int nkc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nk, ((size_t)4 << 30) / per_k));
     ENSURE(gw, uint8_t, "grid_work_emu", zgemm_emu_work_bytes(np, ng, nao, nkc));
@@ -732,7 +733,12 @@ int isdf_fit_zeta(isdf_handle* h, double solve_tol, int32_t* rank_out) {
     CK(zgemm(h->st, 'R', 'N', np, ng, nao, one, X, nao, (int64_t)np * nao, phi, ng, (int64_t)nao * ng, zero, eta,
              ng, (int64_t)np * ng, nk));
   }
-  CK(kdft_cols(h->st, eta, (int64_t)np * ng, km, +1, -1, 1, 1.0 / nk));
+  // the k-convolution of Algorithm 1 over the grid columns: FP64 in the FP64 path,
+  // float-float (~2^-44 relative, FP32 arithmetic) in the others
+  if (h->prec == ISDF_FP64)
+    CK(kdft_cols(h->st, eta, (int64_t)np * ng, km, +1, -1, 1, 1.0 / nk));
+  else
+    CK(kdft_cols_zff(h->st, eta, (int64_t)np * ng, km, +1, -1, 1, 1.0 / nk));
   // Pi^q = L L^H (pivoted), W = L_S^{-1}
   ENSURE(LtPi, double2, "LtPi", (size_t)nk * np * np);
   ENSURE(permPi, int32_t, "permPi", (size_t)nk * np);
@@ -806,26 +812,33 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
   ENSURE(gwork, uint8_t, "grid_work", grid_coulomb_work_bytes(nk, h->cell));
   const int64_t pp = (int64_t)np * np, xg = (int64_t)rx * ng;
   CK(cudaMemsetAsync(Vxi, 0, sizeof(double2) * (size_t)nk * pp, h->st));
-  if (h->prec == ISDF_FP64) {
+  // FP64 and FP64_TC: FP64 arithmetic (an error in V_xi reaches E unamplified, as
+  // P dV_xi P^H with P = M W^T well scaled, so FP64_TC needs more than four slices here)
+  if (h->prec != ISDF_MIXED) {
     for (const auto& r : qh.runs) {
       CK(grid_coulomb_fft(h->st, xi + r.first * xg, rx, r.first, r.second, h->cell, tw, gwork));
       CK(zgemm(h->st, 'R', 'T', rx, rx, ng, make_double2(h->volume, 0.0), xi + r.first * xg, ng, xg,
                xi + r.first * xg, ng, xg, zero, Vxi + r.first * pp, np, pp, r.second));
     }
   } else {
-    // V_xi in complex64 with compensated accumulation: xi is well scaled (|xi| ~ |rho|), and
-    // an error in V_xi reaches E as P dV_xi P^H with P = M W^T well scaled, i.e. relative to
-    // |E| (the ill-conditioned factor W is applied afterwards, in FP64).
-    ENSURE(xif, float2, "xi_f", (size_t)nk * xg);
-    ENSURE(Vxif, float2, "Vxi_f", (size_t)nk * np * np);
-    CK(cudaMemsetAsync(Vxif, 0, sizeof(float2) * (size_t)nk * pp, h->st));
+    // mixed: xi rows to float-float in place, the grid FFT in float-float, and
+    // V_xi = Omega conj(c')c'^T on the tensor cores with four exact slices (~2^-28 relative;
+    // an FP32 FFT and GEMM put ~2e-7 into V_xi, which reaches E and the traces as such)
+    ENSURE(tcw, int, "tc_words", 4);
+    CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
+    const int qcv = vxi_tc_chunk(rx, ng, (size_t)4 << 30);
+    ENSURE(vwork, uint8_t, "grid_work_v", vxi_tc_work_bytes(rx, ng, qcv));
     for (const auto& r : qh.runs) {
-      CK(z2c(h->st, xi + r.first * xg, xif + r.first * xg, r.second * xg));
-      CK(grid_coulomb_fft_f(h->st, xif + r.first * xg, rx, r.first, r.second, h->cell, tw, gwork));
-      CK(cgemm(h->st, 'R', 'T', rx, rx, ng, make_float2((float)h->volume, 0.f), xif + r.first * xg, ng, xg,
-               xif + r.first * xg, ng, xg, make_float2(0.f, 0.f), Vxif + r.first * pp, np, pp, r.second));
-      CK(c2z(h->st, Vxif + r.first * pp, Vxi + r.first * pp, r.second * pp));
+      ffcomplex* xf = reinterpret_cast<ffcomplex*>(xi + r.first * xg);
+      CK(z2ff(h->st, xi + r.first * xg, xf, r.second * xg));
+      CK(grid_coulomb_fft_ff(h->st, xf, rx, r.first, r.second, h->cell, tw, gwork));
+      CK(vxi_tc(h->st, xf, xg, rx, ng, r.second, h->volume, Vxi + r.first * pp, np, pp, vwork, qcv, tcw + 1));
     }
+    int tc_err = 0;
+    CK(cudaMemcpyAsync(&tc_err, tcw + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (tc_err != 0)
+      return fail(h, ISDF_ERR_TIMEOUT, "tensor-core Coulomb GEMM: bounded device wait expired (code %d)", tc_err);
   }
   if (!qh.mirror.empty()) {
     ENSURE(mir, int2, "q_mirror", qh.mirror.size());
@@ -942,7 +955,10 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
   ENSURE(tcw, int, "tc_words", 4);
   CK(cudaMemsetAsync(trall, 0, sizeof(double) * 4 * (size_t)n_frag, h->st));
   CK(cudaMemsetAsync(tcw, 0, 4 * sizeof(int), h->st));
-  if (!mixed) {
+  // FP64_TC: the grouped tensor-core path in float-float with more exact slices,
+  // where B = M L fits its exact accumulation (2 r_q <= 576); else FP64 arithmetic
+  const bool tc64 = (h->prec == ISDF_FP64_TC) && mlgemm5_tc_supported(rp);
+  if (!mixed && !tc64) {
     for (int f = 0; f < n_frag; ++f) {
       const int nf = n_orb[f];
       const int64_t n2 = (int64_t)nf * nf;
@@ -990,18 +1006,25 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     }
   } else {
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-    float2* Xf = (float2*)h->buf("X_f");
-    // B = M L on the tensor cores (four exact slices) when the 2 r_q gathered
-    // columns fit their exact accumulation, else on the compensated SIMT GEMM
-    const bool tc_ml = mlgemm_tc_supported(rp);
+    float2* Xf = tc64 ? nullptr : (float2*)h->buf("X_f");
+    const double2* Xz = (const double2*)h->buf("X");
+    // element bytes of the pair rows Z (float / float-float) and of M^q, B^q
+    const size_t zsz = tc64 ? sizeof(ffloat) : sizeof(float), msz = tc64 ? sizeof(ffcomplex) : sizeof(float2);
+    // B = M L on the tensor cores (four exact slices; five in FP64_TC) when the
+    // 2 r_q gathered columns fit their exact accumulation, else on the
+    // compensated SIMT GEMM
+    const bool tc_ml = tc64 || mlgemm_tc_supported(rp);
     float2* Lwf = nullptr;
     void* lsl = nullptr;
     int* lexp = nullptr;
     if (tc_ml) {
-      lsl = h->ensure_evict("frag_Lsl", mlgemm_tc_lslice_bytes(nk, rp, nj));
+      lsl = h->ensure_evict("frag_Lsl", tc64 ? mlgemm5_tc_lslice_bytes(nk, rp, nj) : mlgemm_tc_lslice_bytes(nk, rp, nj));
       lexp = (int*)h->ensure_evict("frag_Lexp", sizeof(int) * (size_t)nk * mlgemm_tc_nj_pad(nj));
       if (!lsl || !lexp) return fail(h, ISDF_ERR_OOM, "device allocation of the slices of L failed");
-      CK(mlgemm_tc_prepare(h->st, Lq, swd, nk, np, permPi, rankPi, rp, nj, lsl, lexp));
+      if (tc64)
+        CK(mlgemm5_tc_prepare(h->st, Lq, swd, nk, np, permPi, rankPi, rp, nj, lsl, lexp));
+      else
+        CK(mlgemm_tc_prepare(h->st, Lq, swd, nk, np, permPi, rankPi, rp, nj, lsl, lexp));
     } else {
       Lwf = (float2*)h->ensure_evict("frag_Lwf", sizeof(float2) * (size_t)nk * pp);
       if (!Lwf) return fail(h, ISDF_ERR_OOM, "device allocation of frag_Lwf failed");
@@ -1015,7 +1038,7 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     // their rows stacked (each block padded to a tile boundary) so that one launch
     // of each kernel covers the group and the tiles of all its diagonal blocks;
     // a group never needs more scratch than the largest fragment alone.
-    const std::vector<std::vector<int>> groups = fragment_groups(n_frag, n_orb, nk, nS, np);
+    const std::vector<std::vector<int>> groups = fragment_groups(n_frag, n_orb, nk, nS, np, tc64 ? 2.0 : 1.0);
     for (const auto& grp : groups) {
       // rows of each fragment inside the stacked block; padding rows are zero
       std::vector<int64_t> row0(grp.size());
@@ -1036,12 +1059,17 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         flops5 += 2.0 * (double)n2f * (double)(n2f + 1) * sum_nv;
       }
       const int64_t n2max = (int64_t)nfmax * nfmax;
-      ENSURE(Cff, float2, "frag_Cf", (size_t)nk * nao * nfmax);
-      ENSURE(T, float2, "frag_T", (size_t)nk * np * nfmax);
+      // T^k = X^k C^k: complex64 (mixed) or complex128 then float-float in place (FP64_TC)
+      ENSURE(Cff, float2, "frag_Cf", tc64 ? 1 : (size_t)nk * nao * nfmax);
+      ENSURE(T, float2, "frag_T", (size_t)nk * np * nfmax * (tc64 ? 2 : 1));
       // real pair rows Z(R) of the time-reversal basis, and M^q (then B^q) of the
       // q of the sum, stored by their position in it
-      ENSURE(Zr, float, "frag_Zr", (size_t)nk * sq);
-      ENSURE(M, float2, "frag_Mf", (size_t)nS * sq);
+      ENSURE(Zr, uint8_t, "frag_Zr", zsz * (size_t)nk * sq);
+      ENSURE(M, uint8_t, "frag_Mf", msz * (size_t)nS * sq);
+      float* Zr_f = reinterpret_cast<float*>(Zr);
+      ffloat* Zr_ff = reinterpret_cast<ffloat*>(Zr);
+      float2* M_f = reinterpret_cast<float2*>(M);
+      ffcomplex* M_ff = reinterpret_cast<ffcomplex*>(M);
       ENSURE(trpart, double2, "frag_traces_part", std::max<size_t>(2 * (size_t)n2max, syrk_tc_eri_part_count()));
       // tiles of every fragment's diagonal block, in the autotuned band order
       std::vector<int2>& tl = h->tiles_host;
@@ -1075,10 +1103,16 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
       // path, np through Bc on the SIMT path), qc q-points at a time; E' then
       // takes the rows of B^q in chunks of qc positions (fp16 slices of 2 qc nj
       // columns).  qc fits both slice buffers in the workspace limit.
-      const size_t per_q = std::max(syrk_tc_split_bytes(rows, nj), tc_ml ? mlgemm_tc_split_bytes(rows, rp, 1) : 0);
+      auto syrk_split_bytes = [&](int64_t kc) {
+        return tc64 ? syrk4_tc_split_bytes(rows, kc) : syrk_tc_split_bytes(rows, kc);
+      };
+      auto ml_split_bytes = [&](int nq) -> size_t {
+        if (!tc_ml) return 0;
+        return tc64 ? mlgemm5_tc_split_bytes(rows, rp, nq) : mlgemm_tc_split_bytes(rows, rp, nq);
+      };
+      const size_t per_q = std::max(syrk_split_bytes(nj), ml_split_bytes(1));
       const int qc = (int)std::max<int64_t>(1, std::min<int64_t>(nS, (int64_t)(h->split_budget / per_q)));
-      ENSURE(split, uint8_t, "tc_split",
-             std::max(syrk_tc_split_bytes(rows, (int64_t)qc * nj), tc_ml ? mlgemm_tc_split_bytes(rows, rp, qc) : 0));
+      ENSURE(split, uint8_t, "tc_split", std::max(syrk_split_bytes((int64_t)qc * nj), ml_split_bytes(qc)));
       float2* Bc = nullptr;
       if (!tc_ml) {
         Bc = (float2*)h->ensure_evict("frag_Bc", sizeof(float2) * (size_t)qc * sq);
@@ -1097,28 +1131,56 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         for (size_t i = 0; i < grp.size(); ++i) {
           const int f = grp[i], nf = n_orb[f];
           const int64_t n2f = (int64_t)nf * nf;
-          CK(z2c(h->st, (const double2*)C[f], Cff, (int64_t)nk * nao * nf));
-          CK(cgemm(h->st, 'N', 'N', np, nf, nao, one, Xf, nao, (int64_t)np * nao, Cff, nf, (int64_t)nao * nf, zero,
-                   T, nf, (int64_t)np * nf, nk));
-          CK(kdft_cols_f(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.f));
-          // pair rows in the time-reversal basis are real: Z(R) in FP32
-          CK(pair_products_real_f(h->st, T, nk, np, nf, Zr, row0[i], rows));
+          if (tc64) {
+            // T = X C FP64-class (tensor cores, seven exact slices; FP64 beyond N_AO = 64),
+            // then float-float in place for the DFT and the pair rows
+            double2* Tz = reinterpret_cast<double2*>(T);
+            if (zgemm_emu_supported(nao)) {
+              ENSURE(tew, uint8_t, "frag_T_emu", zgemm_emu_work_bytes(np, nfmax, nao, nk));
+              CK(zgemm_emu(h->st, 'N', np, nf, nao, Xz, nao, (int64_t)np * nao, (const double2*)C[f], nf,
+                           (int64_t)nao * nf, Tz, nf, (int64_t)np * nf, nk, tew, tcw + 1));
+            } else {
+              CK(zgemm(h->st, 'N', 'N', np, nf, nao, make_double2(1.0, 0.0), Xz, nao, (int64_t)np * nao,
+                       (const double2*)C[f], nf, (int64_t)nao * nf, make_double2(0.0, 0.0), Tz, nf,
+                       (int64_t)np * nf, nk));
+            }
+            ffcomplex* Tff = reinterpret_cast<ffcomplex*>(Tz);
+            CK(z2ff(h->st, Tz, Tff, (int64_t)nk * np * nf));
+            CK(kdft_cols_ff(h->st, Tff, (int64_t)np * nf, km, +1, +1, 0, 1.0));
+            CK(pair_products_real_ff(h->st, Tff, nk, np, nf, Zr_ff, row0[i], rows));
+          } else {
+            CK(z2c(h->st, (const double2*)C[f], Cff, (int64_t)nk * nao * nf));
+            CK(cgemm(h->st, 'N', 'N', np, nf, nao, one, Xf, nao, (int64_t)np * nao, Cff, nf, (int64_t)nao * nf,
+                     zero, T, nf, (int64_t)np * nf, nk));
+            CK(kdft_cols_f(h->st, T, (int64_t)np * nf, km, +1, +1, 0, 1.f));
+            // pair rows in the time-reversal basis are real: Z(R) in FP32
+            CK(pair_products_real_f(h->st, T, nk, np, nf, Zr_f, row0[i], rows));
+          }
           const int64_t pad = (i + 1 < grp.size()) ? row0[i + 1] - row0[i] - n2f : 0;
           if (pad > 0)
-            CK(cudaMemset2DAsync(Zr + (row0[i] + n2f) * np, sizeof(float) * (size_t)sq, 0,
-                                 sizeof(float) * (size_t)(pad * np), nk, h->st));
+            CK(cudaMemset2DAsync(Zr + zsz * (size_t)((row0[i] + n2f) * np), zsz * (size_t)sq, 0,
+                                 zsz * (size_t)(pad * np), nk, h->st));
         }
         // the R -> q DFT keeps only the q of the sum (M^{-q} = conj(M^q))
-        CK(kdft_real_f(h->st, Zr, M, sq, km, +1, 1.f / nk, qslot_d));
+        if (tc64)
+          CK(kdft_real_ff(h->st, Zr_ff, M_ff, sq, km, +1, 1.0 / nk, qslot_d));
+        else
+          CK(kdft_real_f(h->st, Zr_f, M_f, sq, km, +1, 1.f / nk, qslot_d));
       }
       {
         StageTimer stt(h, 4, flops4);
-        if (tc_ml) {
+        if (tc64) {
+          // as below, five exact slices of the float-float M and of L, B in float-float
+          CK(mlgemm5_tc_rowscale(h->st, M_ff, sq, np, qmap, nS, permPi, rankPi, rp, rows, rexp));
+          for (int j0 = 0; j0 < nS; j0 += qc)
+            CK(mlgemm5_tc_chunk(h->st, M_ff, sq, qmap, rows, np, permPi, rankPi, rp, nj, j0, std::min(qc, nS - j0),
+                                rexp, split, lsl, lexp, nk, tcw + 1));
+        } else if (tc_ml) {
           // row exponents of the gathered M over the q of the sum, then B^q = M^q L^q
           // over M^q, q-chunk by q-chunk
-          CK(mlgemm_tc_rowscale(h->st, M, sq, np, qmap, nS, permPi, rankPi, rp, rows, rexp));
+          CK(mlgemm_tc_rowscale(h->st, M_f, sq, np, qmap, nS, permPi, rankPi, rp, rows, rexp));
           for (int j0 = 0; j0 < nS; j0 += qc)
-            CK(mlgemm_tc_chunk(h->st, M, sq, qmap, rows, np, permPi, rankPi, rp, nj, j0, std::min(qc, nS - j0),
+            CK(mlgemm_tc_chunk(h->st, M_f, sq, qmap, rows, np, permPi, rankPi, rp, nj, j0, std::min(qc, nS - j0),
                                rexp, split, lsl, lexp, nk, tcw + 1));
         } else {
           // consecutive q of a run sit at consecutive positions
@@ -1126,9 +1188,9 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
             for (int q0 = r.first; q0 < r.first + r.second; q0 += qc) {
               const int nq = std::min(qc, r.first + r.second - q0);
               const int64_t j = slot[q0];
-              CK(cgemm(h->st, 'N', 'N', (int)rows, np, np, one, M + j * sq, np, sq, Lwf + q0 * pp, np, pp, zero, Bc,
-                       np, sq, nq));
-              CK(cudaMemcpyAsync(M + j * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice,
+              CK(cgemm(h->st, 'N', 'N', (int)rows, np, np, one, M_f + j * sq, np, sq, Lwf + q0 * pp, np, pp, zero,
+                       Bc, np, sq, nq));
+              CK(cudaMemcpyAsync(M_f + j * sq, Bc, sizeof(float2) * (size_t)nq * sq, cudaMemcpyDeviceToDevice,
                                  h->st));
             }
         }
@@ -1138,15 +1200,22 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         // time-reversal basis (real symmetric, lower-triangle tiles of each diagonal block),
         // then E = W E' W^H per fragment; c = 2 with the pairing, 1 over every q
         StageTimer stt(h, 5, flops5);
-        CK(syrk_tc_rowscale(h->st, M, sq, ldB, nj, nullptr, nS, rows, rexp));
+        if (tc64)
+          CK(syrk4_tc_rowscale(h->st, M_ff, sq, ldB, nj, nS, rows, rexp));
+        else
+          CK(syrk_tc_rowscale(h->st, M_f, sq, ldB, nj, nullptr, nS, rows, rexp));
+        // per-row sums of the left-out diagonal products, accumulated chunk by chunk
+        ENSURE(dcorr, double, "tc_diag_corr", rows);
+        CK(cudaMemsetAsync(dcorr, 0, sizeof(double) * (size_t)rows, h->st));
         const int nq0 = std::min(qc, nS);
-        const TileSchedule sch = tuned_schedule(h, (int64_t)tl.size(), [&](int cfg, int b) -> int {
+        // FP64_TC has one pipeline (no tuning); the band order of the mixed default
+        const TileSchedule sch = tc64 ? TileSchedule{0, 12} : tuned_schedule(h, (int64_t)tl.size(), [&](int cfg, int b) -> int {
           build_tiles(b);
           if (cudaMemcpyAsync(tiles_d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st) !=
               cudaSuccess)
             return -1;
-          return syrk_tc_chunk(h->st, M, sq, ldB, nj, nullptr, rows, 0, nq0, rexp, split, tiles_d, (int)tl.size(),
-                               ws, 0, tcw + 1, cfg) == cudaSuccess ? 0 : -1;
+          return syrk_tc_chunk(h->st, M_f, sq, ldB, nj, nullptr, rows, 0, nq0, rexp, split, tiles_d,
+                               (int)tl.size(), ws, 0, tcw + 1, cfg) == cudaSuccess ? 0 : -1;
         });
         if (sch.band < 0) return fail(h, ISDF_ERR_CUDA, "tile-schedule tuning launch failed");
         build_tiles(sch.band);
@@ -1154,17 +1223,32 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
         CK(cudaMemcpyAsync(tile_of_d, tof.data(), tof.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
         for (int j0 = 0; j0 < nS; j0 += qc) {
           const int nq = std::min(qc, nS - j0);
-          CK(syrk_tc_chunk(h->st, M, sq, ldB, nj, nullptr, rows, j0, nq, rexp, split, tiles_d, (int)tl.size(), ws,
-                           j0 > 0, tcw + 1, sch.cfg));
+          double nv_chunk = 0.0;  // the chunk's share of the algorithmic flops
+          for (int j = j0; j < j0 + nq; ++j) nv_chunk += h->ranks_v[qs[j]];
+          if (tc64) {
+            CK(syrk4_tc_split(h->st, M_ff, sq, ldB, nj, rows, j0, nq, rexp, split, dcorr));
+            StageTimer stk(h, 6, flops5 * nv_chunk / std::max(sum_nv, 1.0));
+            CK(syrk4_tc_mma(h->st, split, rows, nq, nj, tiles_d, (int)tl.size(), ws, j0 > 0, tcw + 1));
+          } else {
+            CK(syrk_tc_split(h->st, M_f, sq, ldB, nj, nullptr, rows, j0, nq, rexp, split, dcorr));
+            StageTimer stk(h, 6, flops5 * nv_chunk / std::max(sum_nv, 1.0));
+            CK(syrk_tc_mma(h->st, split, rows, nq, nj, tiles_d, (int)tl.size(), ws, j0 > 0, tcw + 1, sch.cfg));
+          }
         }
         // E = W E' W^H per fragment, written straight to the caller's ERIs (chemist's
         // order) with the FP64 traces accumulated on the way
         for (size_t i = 0; i < grp.size(); ++i) {
           const int f = grp[i];
-          CK(syrk_tc_finish_eri(h->st, ws, (int)tl.size(), tile_of_d + tof_off[i], orb_d + orb_off[i], n_orb[f],
-                                rexp + row0[i], (h->q_sym ? 2.0 : 1.0) / nk,
-                                eri_out ? (float2*)eri_out[f] : nullptr,
-                                any_tr ? (const double2*)gamma[f] : nullptr, trpart, trall + 4 * (int64_t)f));
+          const double sc = (h->q_sym ? 2.0 : 1.0) / nk;
+          const double2* gf = any_tr ? (const double2*)gamma[f] : nullptr;
+          if (tc64)
+            CK(syrk_tc_finish_eri_z(h->st, ws, (int)tl.size(), tile_of_d + tof_off[i], orb_d + orb_off[i],
+                                    n_orb[f], rexp + row0[i], dcorr + row0[i], sc,
+                                    eri_out ? (double2*)eri_out[f] : nullptr, gf, trpart, trall + 4 * (int64_t)f));
+          else
+            CK(syrk_tc_finish_eri(h->st, ws, (int)tl.size(), tile_of_d + tof_off[i], orb_d + orb_off[i], n_orb[f],
+                                  rexp + row0[i], dcorr + row0[i], sc, eri_out ? (float2*)eri_out[f] : nullptr, gf,
+                                  trpart, trall + 4 * (int64_t)f));
         }
       }
     }

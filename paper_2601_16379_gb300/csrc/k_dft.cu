@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace isdf {
 
@@ -30,6 +31,25 @@ template <>
 struct CT<float2> {
   using R = float;
   __device__ static float2 mk(float a, float b) { return make_float2(a, b); }
+};
+// float-float complex: the FP64-class path's transforms in FP32 arithmetic
+template <>
+struct CT<ffcomplex> {
+  using R = ffloat;
+  __device__ static ffcomplex mk(ffloat a, ffloat b) { return ffcomplex{a, b}; }
+};
+
+// Storage <-> working type of a transform: the same type, or complex128 data
+// transformed in float-float.
+template <typename T, typename TS>
+struct Cv {
+  __device__ static T in(const TS& v) { return v; }
+  __device__ static TS out(const T& v) { return v; }
+};
+template <>
+struct Cv<ffcomplex, double2> {
+  __device__ static ffcomplex in(const double2& v) { return ffcomplex{ffloat(v.x), ffloat(v.y)}; }
+  __device__ static double2 out(const ffcomplex& v) { return make_double2(v.x.to_double(), v.y.to_double()); }
 };
 
 struct Twiddles16 {
@@ -273,8 +293,8 @@ __device__ void kmesh_dft_cubic(T* s, int lct, int padk, const typename CT<T>::R
   }
 }
 
-template <typename T, int L>
-__global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, int64_t ncol, int lct, int padk,
+template <typename T, int L, typename TS = T>
+__global__ void __launch_bounds__(256) kdft_cubic_kernel(TS* __restrict__ data, int64_t ncol, int lct, int padk,
                                                          int mode, Twiddles16 tw1, Twiddles16 tw2, double scale) {
   using R = typename CT<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -293,7 +313,7 @@ __global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, i
     const int k = e >> lct, c = e & (ct - 1);
     const int64_t col = c0 + c;
     T v = CT<T>::mk(0, 0);
-    if (col < ncol) v = data[(int64_t)k * ncol + col];
+    if (col < ncol) v = Cv<T, TS>::in(data[(int64_t)k * ncol + col]);
     s[cidx<T, L>(k, c, lct, padk)] = v;
   }
   __syncthreads();
@@ -312,7 +332,7 @@ __global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, i
     const int64_t col = c0 + c;
     if (col < ncol) {
       const T v = s[cidx<T, L>(k, c, lct, padk)];
-      data[(int64_t)k * ncol + col] = CT<T>::mk(v.x * (R)scale, v.y * (R)scale);
+      data[(int64_t)k * ncol + col] = Cv<T, TS>::out(CT<T>::mk(v.x * (R)scale, v.y * (R)scale));
     }
   }
 }
@@ -320,15 +340,17 @@ __global__ void __launch_bounds__(256) kdft_cubic_kernel(T* __restrict__ data, i
 // DFT along the k-mesh of real columns, out of place, keeping the q with
 // qslot[q] >= 0:  out[qslot[q]][col] = scale sum_k e^{s 2 pi i m_q.m_k/n} in[k][col].
 // The real pair rows of the time-reversal basis give M^{-q} = conj(M^q), so
-// the half set of q in qslot carries all of it.  Two real columns x, y share
-// one complex working column z = x + i y (a block holds 2 ct real columns, so
-// each k-row of the input is read 2 ct floats at a time); after the transform
-// X(q) = (Z(q) + conj(Z(-q)))/2 and Y(q) = (Z(q) - conj(Z(-q)))/(2i).
+// the half set of q in qslot carries all of it.  Two adjacent real columns x =
+// col 2c, y = col 2c + 1 share one complex working column z = x + i y, so a row
+// of the shared working array is a plain copy of an input row (loaded as
+// 16-byte vectors, eight in flight per thread); after the transform
+// X(q) = (Z(q) + conj(Z(-q)))/2 and Y(q) = (Z(q) - conj(Z(-q)))/(2i), written
+// side by side.
 template <typename T, int L>
 __global__ void __launch_bounds__(256) kdft_real_cubic_kernel(const typename CT<T>::R* __restrict__ in,
                                                               T* __restrict__ out, int64_t ncol, int lct, int padk,
                                                               const int* __restrict__ qslot, Twiddles16 tw,
-                                                              double scale) {
+                                                              double scale, int vec) {
   using R = typename CT<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
@@ -340,27 +362,59 @@ __global__ void __launch_bounds__(256) kdft_real_cubic_kernel(const typename CT<
   constexpr int nk = L * L * L;
   const int ct = 1 << lct;
   const int64_t c0 = (int64_t)blockIdx.x << (lct + 1);  // 2 ct real columns per block
-  for (int e = threadIdx.x; e < nk * 2 * ct; e += blockDim.x) {
-    const int k = e >> (lct + 1), c2 = e & (2 * ct - 1);
-    const int64_t col = c0 + c2;
-    const R v = (col < ncol) ? in[(int64_t)k * ncol + col] : (R)0;
-    // column c2 < ct is the real part of working column c2, else the imaginary part of c2 - ct
-    R* w = reinterpret_cast<R*>(&s[cidx<T, L>(k, c2 & (ct - 1), lct, padk)]);
-    w[c2 >> lct] = v;
+  if (vec) {
+    // 16-byte vectors: EPV working columns each; every vector lies wholly inside or
+    // outside [0, ncol) (ncol and c0 are multiples of 2 EPV)
+    constexpr int EPV = 16 / (int)sizeof(T);
+    const int vpr = ct / EPV, total = nk * vpr;
+    constexpr int kBatch = 8;
+    for (int b0 = threadIdx.x; b0 < total; b0 += 256 * kBatch) {
+      float4 buf[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int v = b0 + u * 256;
+        buf[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v < total) {
+          const int k = v / vpr, cv = v % vpr;
+          const int64_t col = c0 + 2 * (int64_t)cv * EPV;
+          if (col < ncol) buf[u] = __ldg(reinterpret_cast<const float4*>(in + (int64_t)k * ncol + col));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int v = b0 + u * 256;
+        if (v < total) {
+          const int k = v / vpr, cv = v % vpr;
+          const T* e = reinterpret_cast<const T*>(&buf[u]);
+#pragma unroll
+          for (int i = 0; i < EPV; ++i) s[cidx<T, L>(k, cv * EPV + i, lct, padk)] = e[i];
+        }
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < nk * 2 * ct; e += blockDim.x) {
+      const int k = e >> (lct + 1), c2 = e & (2 * ct - 1);
+      const int64_t col = c0 + c2;
+      const R v = (col < ncol) ? in[(int64_t)k * ncol + col] : (R)0;
+      // column 2c is the real part of working column c, column 2c + 1 the imaginary part
+      R* w = reinterpret_cast<R*>(&s[cidx<T, L>(k, c2 >> 1, lct, padk)]);
+      w[c2 & 1] = v;
+    }
   }
   __syncthreads();
   kmesh_dft_cubic<T, L>(s, lct, padk, twc, tws);
   const R h = (R)(0.5 * scale);
-  for (int e = threadIdx.x; e < nk * 2 * ct; e += blockDim.x) {
-    const int k = e >> (lct + 1), c2 = e & (2 * ct - 1), c = c2 & (ct - 1);
-    const int64_t col = c0 + c2;
+  for (int e = threadIdx.x; e < nk * ct; e += blockDim.x) {
+    const int k = e >> lct, c = e & (ct - 1);
+    const int64_t col = c0 + 2 * (int64_t)c;
     const int j = qslot[k];
     if (col < ncol && j >= 0) {
       const int m0 = k / (L * L), m1 = (k / L) % L, m2 = k % L;
       const int km = (((L - m0) % L) * L + (L - m1) % L) * L + (L - m2) % L;
       const T zq = s[cidx<T, L>(k, c, lct, padk)], zm = s[cidx<T, L>(km, c, lct, padk)];
-      out[(int64_t)j * ncol + col] = (c2 < ct) ? CT<T>::mk(h * (zq.x + zm.x), h * (zq.y - zm.y))
-                                               : CT<T>::mk(h * (zq.y + zm.y), h * (zm.x - zq.x));
+      T* o = out + (int64_t)j * ncol + col;
+      o[0] = CT<T>::mk(h * (zq.x + zm.x), h * (zq.y - zm.y));
+      if (col + 1 < ncol) o[1] = CT<T>::mk(h * (zq.y + zm.y), h * (zm.x - zq.x));
     }
   }
 }
@@ -412,8 +466,8 @@ inline int kdft_cubic_pad(int L, int ct, int elem) {
   return (((ct - L * ct) % G) + G) % G;
 }
 
-template <typename T, int L>
-cudaError_t kdft_cubic_launch(cudaStream_t st, T* data, int64_t ncol, int mode, const Twiddles16& t1,
+template <typename T, int L, typename TS = T>
+cudaError_t kdft_cubic_launch(cudaStream_t st, TS* data, int64_t ncol, int mode, const Twiddles16& t1,
                               const Twiddles16& t2, double scale) {
   constexpr int nk = L * L * L;
   int lct = 0;
@@ -421,13 +475,13 @@ cudaError_t kdft_cubic_launch(cudaStream_t st, T* data, int64_t ncol, int mode, 
   const int padk = kdft_cubic_pad(L, 1 << lct, (int)sizeof(T));
   const size_t smem = ((size_t)nk << lct) * sizeof(T) + (size_t)(nk / L) * padk * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kdft_cubic_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(kdft_cubic_kernel<T, L, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t nblk = (ncol + (1 << lct) - 1) >> lct;
   if (nblk > 2147483647LL) return cudaErrorInvalidValue;
-  kdft_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, lct, padk, mode, t1, t2, scale);
+  kdft_cubic_kernel<T, L, TS><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, lct, padk, mode, t1, t2, scale);
   count_launch();
   return cudaGetLastError();
 }
@@ -447,13 +501,18 @@ cudaError_t kdft_real_cubic_launch(cudaStream_t st, const typename CT<T>::R* in,
   }
   const int64_t nblk = (ncol + (2 << lct) - 1) >> (lct + 1);  // 2 ct real columns per block
   if (nblk > 2147483647LL) return cudaErrorInvalidValue;
-  kdft_real_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(in, out, ncol, lct, padk, qslot, tw, scale);
+  // 16-byte vector loads when every row starts 16-byte aligned and a vector never
+  // straddles the end of a row
+  constexpr int kEpv = 16 / (int)sizeof(T);
+  const int vec = ((reinterpret_cast<uintptr_t>(in) & 15) == 0 && (ncol % (2 * kEpv)) == 0 &&
+                   (1 << lct) % kEpv == 0) ? 1 : 0;
+  kdft_real_cubic_kernel<T, L><<<(unsigned)nblk, 256, smem, st>>>(in, out, ncol, lct, padk, qslot, tw, scale, vec);
   count_launch();
   return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) kdft_cols_kernel(T* __restrict__ data, int64_t ncol, KMesh km,
+template <typename T, typename TS = T>
+__global__ void __launch_bounds__(256) kdft_cols_kernel(TS* __restrict__ data, int64_t ncol, KMesh km,
                                                         int ct, int mode, Twiddles16 tw1,
                                                         Twiddles16 tw2, double scale) {
   using R = typename CT<T>::R;
@@ -472,7 +531,7 @@ __global__ void __launch_bounds__(256) kdft_cols_kernel(T* __restrict__ data, in
     const int k = e / ct, c = e % ct;
     const int64_t col = c0 + c;
     T v = CT<T>::mk(0, 0);
-    if (col < ncol) v = data[(int64_t)k * ncol + col];
+    if (col < ncol) v = Cv<T, TS>::in(data[(int64_t)k * ncol + col]);
     s[e] = v;
   }
   __syncthreads();
@@ -490,13 +549,13 @@ __global__ void __launch_bounds__(256) kdft_cols_kernel(T* __restrict__ data, in
     const int64_t col = c0 + c;
     if (col < ncol) {
       T v = s[e];
-      data[(int64_t)k * ncol + col] = CT<T>::mk(v.x * (R)scale, v.y * (R)scale);
+      data[(int64_t)k * ncol + col] = Cv<T, TS>::out(CT<T>::mk(v.x * (R)scale, v.y * (R)scale));
     }
   }
 }
 
-template <typename T>
-cudaError_t kdft_launch(cudaStream_t st, T* data, int64_t ncol, KMesh km, int s1, int s2, int mode,
+template <typename T, typename TS = T>
+cudaError_t kdft_launch(cudaStream_t st, TS* data, int64_t ncol, KMesh km, int s1, int s2, int mode,
                         double scale) {
   const int nk = km.n[0] * km.n[1] * km.n[2];
   for (int a = 0; a < 3; ++a)
@@ -505,12 +564,12 @@ cudaError_t kdft_launch(cudaStream_t st, T* data, int64_t ncol, KMesh km, int s1
   if (km.n[0] == km.n[1] && km.n[1] == km.n[2]) {
     const Twiddles16 t1 = make_tw(km.n, s1), t2 = make_tw(km.n, s2);
     switch (km.n[0]) {
-      case 2: return kdft_cubic_launch<T, 2>(st, data, ncol, mode, t1, t2, scale);
-      case 3: return kdft_cubic_launch<T, 3>(st, data, ncol, mode, t1, t2, scale);
-      case 4: return kdft_cubic_launch<T, 4>(st, data, ncol, mode, t1, t2, scale);
-      case 6: return kdft_cubic_launch<T, 6>(st, data, ncol, mode, t1, t2, scale);
-      case 8: return kdft_cubic_launch<T, 8>(st, data, ncol, mode, t1, t2, scale);
-      case 10: return kdft_cubic_launch<T, 10>(st, data, ncol, mode, t1, t2, scale);
+      case 2: return kdft_cubic_launch<T, 2, TS>(st, data, ncol, mode, t1, t2, scale);
+      case 3: return kdft_cubic_launch<T, 3, TS>(st, data, ncol, mode, t1, t2, scale);
+      case 4: return kdft_cubic_launch<T, 4, TS>(st, data, ncol, mode, t1, t2, scale);
+      case 6: return kdft_cubic_launch<T, 6, TS>(st, data, ncol, mode, t1, t2, scale);
+      case 8: return kdft_cubic_launch<T, 8, TS>(st, data, ncol, mode, t1, t2, scale);
+      case 10: return kdft_cubic_launch<T, 10, TS>(st, data, ncol, mode, t1, t2, scale);
       default: break;
     }
   }
@@ -519,13 +578,13 @@ cudaError_t kdft_launch(cudaStream_t st, T* data, int64_t ncol, KMesh km, int s1
   if (ct > 32) ct = 32;
   size_t smem = (size_t)nk * ct * sizeof(T);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kdft_cols_kernel<T>,
+    cudaError_t e = cudaFuncSetAttribute(kdft_cols_kernel<T, TS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   int64_t nblk = (ncol + ct - 1) / ct;
   if (nblk > 2147483647LL) return cudaErrorInvalidValue;
-  kdft_cols_kernel<T><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, km, ct, mode,
+  kdft_cols_kernel<T, TS><<<(unsigned)nblk, 256, smem, st>>>(data, ncol, km, ct, mode,
                                                          make_tw(km.n, s1), make_tw(km.n, s2), scale);
   count_launch();
   return cudaGetLastError();
@@ -920,6 +979,10 @@ cudaError_t grid_coulomb_fft_f(cudaStream_t st, float2* x, int rows_per_q, int q
                                const CellDev& c, const double2* dtw, void* work) {
   return grid_fft_launch<float2>(st, x, rows_per_q, q0, nq, c, dtw, work);
 }
+cudaError_t grid_coulomb_fft_ff(cudaStream_t st, ffcomplex* x, int rows_per_q, int q0, int nq,
+                                const CellDev& c, const double2* dtw, void* work) {
+  return grid_fft_launch<ffcomplex>(st, x, rows_per_q, q0, nq, c, dtw, work);
+}
 
 void grid_twiddles(const int mesh[3], double2* host192) {
   for (int a = 0; a < 3; ++a)
@@ -930,6 +993,42 @@ void grid_twiddles(const int mesh[3], double2* host192) {
 }
 cudaError_t pair_products(cudaStream_t st, const double2* t, int nk, int np, int nf, double2* Z) {
   return pair_launch<double2>(st, t, nk, np, nf, Z);
+}
+
+// ---- float-float variants (FP64-class tensor-core path)
+namespace {
+__global__ void z2ff_kernel(const double2* __restrict__ in, ffcomplex* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = in[e];
+    out[e] = ffcomplex{ffloat(v.x), ffloat(v.y)};
+  }
+}
+}  // namespace
+
+cudaError_t z2ff(cudaStream_t st, const double2* in, ffcomplex* out, int64_t n) {
+  if (n <= 0) return cudaSuccess;
+  int64_t nb = (n + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;
+  z2ff_kernel<<<(unsigned)nb, 256, 0, st>>>(in, out, n);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t kdft_cols_ff(cudaStream_t st, ffcomplex* data, int64_t ncol, KMesh km, int s1, int s2, int mode,
+                         double scale) {
+  return kdft_launch<ffcomplex>(st, data, ncol, km, s1, s2, mode, scale);
+}
+cudaError_t kdft_cols_zff(cudaStream_t st, double2* data, int64_t ncol, KMesh km, int s1, int s2, int mode,
+                          double scale) {
+  return kdft_launch<ffcomplex, double2>(st, data, ncol, km, s1, s2, mode, scale);
+}
+cudaError_t kdft_real_ff(cudaStream_t st, const ffloat* in, ffcomplex* out, int64_t ncol, KMesh km, int s,
+                         double scale, const int* qslot) {
+  return kdft_real_launch<ffcomplex>(st, in, out, ncol, km, s, scale, qslot);
+}
+cudaError_t pair_products_real_ff(cudaStream_t st, const ffcomplex* t, int nk, int np, int nf, ffloat* Zr,
+                                  int64_t row0, int64_t rows) {
+  if (row0 < 0 || row0 + (int64_t)nf * nf > rows) return cudaErrorInvalidValue;
+  return pair_real_launch<ffcomplex>(st, t, nk, np, nf, Zr, row0, rows);
 }
 
 }  // namespace isdf

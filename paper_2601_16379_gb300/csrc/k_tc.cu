@@ -68,6 +68,9 @@ constexpr int B_BYTES = BN * BK * 2;        // 16 KB per slice
 constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);  // 96 KB
 constexpr int TMEM_COLS = 512;              // g0 (two buffers), g1, g2: four 128-column FP32 accumulators
 constexpr int NTHREADS = 192;
+// E' kernel: warp 0 TMA, warp 1 MMA, 16 drain warps (TMEM lane quarter warp % 4, 32 of
+// the 128 columns each), whose registers hold the tile's float-float running sums
+constexpr int kSyrkThreads = 576, kDrainWarps = 16, kDrainCols = 32;
 constexpr int kChunkKB = 16;                // k-blocks per exact g0 chunk: 64 k-steps of 16
 constexpr int kP1 = 4;                      // chunks per g1 drain
 constexpr int kP2 = 16;                     // chunks per g2 drain
@@ -87,7 +90,7 @@ struct TileArgs {
 // Pipeline variants: BKt fp16 of K per stage row (64: 128-byte swizzle, 32: 64-byte
 // swizzle) and NST stages; a 1024-element exact chunk of g0 is 1024 / BKt k-blocks.
 template <int BKt, int NST>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(kSyrkThreads, 1)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
                    const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mB1,
                    const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, TileArgs args) {
@@ -118,10 +121,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 128);
+      mbar_init(&acce[b], kDrainWarps);
     }
-    mbar_init(acce1, 128);
-    mbar_init(acce2, 128);
+    mbar_init(acce1, kDrainWarps);
+    mbar_init(acce2, kDrainWarps);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -199,70 +202,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {
-    // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4)
-    const int q = warp & 3;
-    const int row = q * 32 + lane;
+    // drain warps 2..17: TMEM lane quarter warp % 4 (a hardware rule), 32 columns each;
+    // the tile's float-float sums stay in registers until the last chunk
+    const int q = warp & 3, cblk = (warp - 2) >> 2;
+    const int row = q * 32 + lane, col0 = cblk * kDrainCols;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     float* __restrict__ wh = args.ws_hi + (size_t)blockIdx.x * BN * BM;
     float* __restrict__ wl = args.ws_lo + (size_t)blockIdx.x * BN * BM;
-    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    float H[kDrainCols], L[kDrainCols];
+#pragma unroll
+    for (int j = 0; j < kDrainCols; ++j) {
+      H[j] = args.accumulate ? wh[(size_t)(col0 + j) * BM + row] : 0.f;
+      L[j] = args.accumulate ? wl[(size_t)(col0 + j) * BM + row] : 0.f;
+    }
+    bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
-      if (!mbar_wait(&accf[c & 1], (c >> 1) & 1, s_err, args.err, 4)) break;
+      ok = __all_sync(0xffffffffu, mbar_wait(&accf[c & 1], (c >> 1) & 1, s_err, args.err, 4));
+      if (!ok) break;
       tc_fence_after();
       const bool last = (c == nchunks - 1);
       const bool drain1 = last || (c % kP1) == kP1 - 1;
       const bool drain2 = last || (c % kP2) == kP2 - 1;
-#pragma unroll 1
-      for (int cb = 0; cb < BN / 32; ++cb) {
-        uint32_t v0[32];
-        float H[32], L[32];
-        const size_t base = (size_t)(cb * 32) * BM + row;
-        const bool fresh = (c == 0) && !args.accumulate;
-        if (!fresh) {
-          // issue all 64 global loads of this column block before the TMEM reads
+      const uint32_t t0 = tmem_base + lane_off + (uint32_t)((c & 1) * BN + col0);
+      const uint32_t t1 = tmem_base + lane_off + (uint32_t)(2 * BN + col0);
+      const uint32_t t2 = tmem_base + lane_off + (uint32_t)(3 * BN + col0);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            H[j] = wh[base + (size_t)j * BM];
-            L[j] = wl[base + (size_t)j * BM];
-          }
-        }
-        tmem_ld32(tmem_base + lane_off + (uint32_t)((c & 1) * BN + cb * 32), v0);
+      for (int cb = 0; cb < kDrainCols / 4; ++cb) {
+        uint32_t v0[4], v1[4], v2[4];
+        tmem_ld4(t0 + cb * 4, v0);
+        if (drain1) tmem_ld4(t1 + cb * 4, v1);
+        if (drain2) tmem_ld4(t2 + cb * 4, v2);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < 4; ++j) {
+          const int jj = cb * 4 + j;
           const float a0 = __uint_as_float(v0[j]);
-          if (fresh) {
-            H[j] = a0;
-            L[j] = 0.f;
-          } else {
-            // (H, L) += a0 with TwoSum on the high part
-            const float S = H[j] + a0;
-            const float bp = S - H[j];
-            const float e = (H[j] - (S - bp)) + (a0 - bp);
-            H[j] = S;
-            L[j] += e;
-          }
-        }
-        if (drain1) {
-          uint32_t v1[32];
-          tmem_ld32(tmem_base + lane_off + (uint32_t)(2 * BN + cb * 32), v1);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) L[j] = fmaf(__uint_as_float(v1[j]), 1.0f / 128.0f, L[j]);
-        }
-        if (drain2) {
-          uint32_t v2[32];
-          tmem_ld32(tmem_base + lane_off + (uint32_t)(3 * BN + cb * 32), v2);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) L[j] = fmaf(__uint_as_float(v2[j]), 1.0f / 16384.0f, L[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          wh[base + (size_t)j * BM] = H[j];
-          wl[base + (size_t)j * BM] = L[j];
+          // (H, L) += a0 with TwoSum on the high part
+          const float S = H[jj] + a0;
+          const float bp = S - H[jj];
+          const float e = (H[jj] - (S - bp)) + (a0 - bp);
+          H[jj] = S;
+          float l = L[jj] + e;
+          if (drain1) l = fmaf(__uint_as_float(v1[j]), 1.0f / 128.0f, l);
+          if (drain2) l = fmaf(__uint_as_float(v2[j]), 1.0f / 16384.0f, l);
+          L[jj] = l;
         }
       }
       tc_fence_before();
-      mbar_arrive(&acce[c & 1]);
-      if (drain1) mbar_arrive(acce1);
-      if (drain2) mbar_arrive(acce2);
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&acce[c & 1]);
+        if (drain1) mbar_arrive(acce1);
+        if (drain2) mbar_arrive(acce2);
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int j = 0; j < kDrainCols; ++j) {
+        wh[(size_t)(col0 + j) * BM + row] = H[j];
+        wl[(size_t)(col0 + j) * BM + row] = L[j];
+      }
     }
   }
   tc_fence_before();
@@ -315,44 +314,76 @@ __global__ void rrow_scale_kernel(BView B, int64_t K, int* __restrict__ row_exp)
   if (threadIdx.x == 0) row_exp[a] = slice_exp(m);
 }
 
-// Three integer slices of the (re, im) pair v 2^ex, written as half2 at S_i[at].
-__device__ __forceinline__ void put3(float2 v, int ex, int64_t at, __half* __restrict__ S1, __half* __restrict__ S2,
-                                     __half* __restrict__ S3) {
-  const float vals[2] = {ldexpf(v.x, ex), ldexpf(v.y, ex)};
-  __half h1[2], h2[2], h3[2];
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const float s1 = rintf(vals[t]);
-    const float r1 = (vals[t] - s1) * 128.f;
-    const float s2 = rintf(r1);
-    const float r2 = (r1 - s2) * 128.f;
-    const float s3 = rintf(r2);
-    h1[t] = __float2half_rn(s1);
-    h2[t] = __float2half_rn(s2);
-    h3[t] = __float2half_rn(s3);
-  }
-  *reinterpret_cast<__half2*>(S1 + at) = __halves2half2(h1[0], h1[1]);
-  *reinterpret_cast<__half2*>(S2 + at) = __halves2half2(h2[0], h2[1]);
-  *reinterpret_cast<__half2*>(S3 + at) = __halves2half2(h3[0], h3[1]);
+// Three integer slices of v 2^ex (|v 2^ex| < 128): v 2^ex = s1 + s2/128 + s3/128^2 + r.
+__device__ __forceinline__ void slice3(float v, int ex, float& s1, float& s2, float& s3) {
+  const float x = ldexpf(v, ex);
+  s1 = rintf(x);
+  const float r1 = (x - s1) * 128.f;
+  s2 = rintf(r1);
+  s3 = rintf((r1 - s2) * 128.f);
 }
 
-// Slices of the R rows for the sum positions j0 .. j0 + nq - 1: row a holds, at
-// columns 2 (jl nJ + J) and + 1, the (re, im) of B at (position j0 + jl, J);
-// columns beyond 2 nq nJ (up to the padded width K2) are zero.
-__global__ void rsplit_kernel(BView B, int64_t n2, int64_t j0, int nq, int64_t K2, const int* __restrict__ row_exp,
-                              __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3) {
-  const int64_t half = K2 / 2, ncol = (int64_t)nq * B.nJ, total = n2 * half;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = e / half, c2 = e - a * half;
+// Slices of the R rows for the sum positions j0 .. j0 + nq - 1, one block per
+// row a: columns 2 (jl nJ + J) and + 1 hold the (re, im) of B at (position
+// j0 + jl, J); columns beyond 2 nq nJ (up to the padded width K2) are zero.
+// With corr, the block also adds to corr[a] the products of the row with itself
+// that the six-product contraction leaves out, 2 s2 s3 / 128^3 + s3^2 / 128^4 per
+// value (in slice units): on E'_aa they are all of one sign, so dropping them
+// biases the diagonal (the off-diagonal ones average out); the finish adds corr.
+__global__ void __launch_bounds__(256) rsplit_kernel(BView B, int64_t j0, int nq, int64_t K2,
+                                                     const int* __restrict__ row_exp, __half* __restrict__ S1,
+                                                     __half* __restrict__ S2, __half* __restrict__ S3,
+                                                     double* __restrict__ corr) {
+  const int64_t a = blockIdx.x, half = K2 / 2, ncol = (int64_t)nq * B.nJ;
+  const int ex = row_exp[a];
+  float d = 0.f;
+  for (int64_t c2 = threadIdx.x; c2 < half; c2 += blockDim.x) {
     const float2 x = (c2 < ncol) ? B.at(a, j0 * B.nJ + c2) : make_float2(0.f, 0.f);
-    put3(x, row_exp[a], a * K2 + 2 * c2, S1, S2, S3);
+    float r1, r2, r3, i1, i2, i3;
+    slice3(x.x, ex, r1, r2, r3);
+    slice3(x.y, ex, i1, i2, i3);
+    const int64_t at = a * K2 + 2 * c2;
+    *reinterpret_cast<__half2*>(S1 + at) = __floats2half2_rn(r1, i1);
+    *reinterpret_cast<__half2*>(S2 + at) = __floats2half2_rn(r2, i2);
+    *reinterpret_cast<__half2*>(S3 + at) = __floats2half2_rn(r3, i3);
+    d += (2.f * (r2 * r3 + i2 * i3) + (r3 * r3 + i3 * i3) * (1.f / 128.f)) * (1.f / 2097152.f);
+  }
+  if (!corr) return;
+  __shared__ double sd[8];
+  double v = d;
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sd[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sd[w];
+    corr[a] += t;
   }
 }
 
-// E'(i, j) (symmetric) from the float-float tile workspace of the lower triangle.
-__device__ __forceinline__ double ep_val(const float* __restrict__ wh, const float* __restrict__ wl,
-                                         const int* __restrict__ tile_of, int nt, int64_t i, int64_t j,
-                                         const int* __restrict__ row_exp, double scale) {
+// The E' -> E map fused with the chemist's permutation and the traces, so that E
+// is never stored.  Orbit o1 (a pair p < q: rows u = 2 o1, v = 2 o1 + 1; or a
+// diagonal p: one row) and orbit o2 (x < y or x) span a block of E':
+// U = E'(u1, u2), X = E'(u1, v2), Y = E'(v1, u2), Z = E'(v1, v2).  Its ERIs are
+//   pair-pair:  (pq|yx) = [(U+Z) + i(Y-X)]/4,  (pq|xy) = [(U-Z) + i(X+Y)]/4,
+//               (qp|yx) = conj (pq|xy),       (qp|xy) = conj (pq|yx);
+//   pair-diag:  (pq|xx) = (U + iY)/2,  (qp|xx) = conj;
+//   diag-pair:  (pp|yx) = (U - iX)/2,  (pp|xy) = conj;     diag-diag: (pp|xx) = U.
+// For a Hermitian gamma the four terms of a block in E_J = 1/2 sum gamma_pq gamma_rs (pq|rs)
+// and E_K = -1/4 sum gamma_ps gamma_rq (pq|rs) pair up into real parts:
+//   J_block = U Re A Re B - Z Im A Im B + X Re A Im B - Y Im A Re B   (A = gamma_pq, B = gamma_yx),
+//   K_block = 2 Re(gamma_px gamma_yq (pq|yx)) + 2 Re(gamma_py gamma_xq (pq|xy)),
+// and the pair-diagonal and diagonal cases likewise, so the traces take a few
+// real FP64 operations per block instead of complex ones per ERI.  Each thread
+// takes one block with o1 >= o2 (consecutive threads: consecutive o1, so the
+// workspace reads of the lower triangle are contiguous) and its mirror (o2, o1),
+// whose values are (U, Y, X, Z).  Values are formed in float-float, the ERIs
+// written as complex64 (mixed) or complex128 (FP64_TC); eri may be NULL, and
+// gamma NULL skips the traces.  Per-block partials go to part[blk] (J) and
+// part[gridDim.x + blk] (K); the fixed grid keeps the sums reproducible.
+__device__ __forceinline__ ffloat ep_ff(const float* __restrict__ wh, const float* __restrict__ wl,
+                                        const int* __restrict__ tile_of, int nt, int64_t i, int64_t j,
+                                        const int* __restrict__ row_exp, ffloat sc) {
   if (i < j) {
     const int64_t t = i;
     i = j;
@@ -360,126 +391,120 @@ __device__ __forceinline__ double ep_val(const float* __restrict__ wh, const flo
   }
   const int t = tile_of[(i / BM) * nt + (j / BN)];
   const size_t base = ((size_t)t * BN + (size_t)(j % BN)) * BM + (size_t)(i % BM);
-  return ((double)wh[base] + (double)wl[base]) * ldexp(scale, -(row_exp[i] + row_exp[j]));
+  const ffloat v = ff_two_sum(wh[base], wl[base]);
+  return ff_ldexp(v, -(row_exp[i] + row_exp[j])) * sc;
 }
 
-// E (complex128 n2 x n2, full) from E' = W^H E W: E = W E' W^H with the
-// unnormalised rows above, i.e. coefficients 1/2 (u) and +-i/2 (v) for pair
-// rows and 1 for diagonal rows.  orb[o] = (p, q): o < P the pairs p < q in
-// lexicographic order (rows 2o, 2o + 1), o = P + p the diagonals (row 2P + p).
-// One thread per orbit pair writes its 1, 2 or 4 entries.
-__global__ void syrk_finish_kernel(const float* __restrict__ wh, const float* __restrict__ wl,
-                                   const int* __restrict__ tile_of, int nt, const int2* __restrict__ orb, int nf,
-                                   const int* __restrict__ row_exp, double scale, double2* __restrict__ E) {
-  const int no = nf * (nf + 1) / 2, P = nf * (nf - 1) / 2;
-  const int64_t n2 = (int64_t)nf * nf, total = (int64_t)no * no;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int o1 = (int)(e / no), o2 = (int)(e % no);
-    const int2 x1 = orb[o1], x2 = orb[o2];
-    const int64_t a = (int64_t)x1.x * nf + x1.y, as = (int64_t)x1.y * nf + x1.x;
-    const int64_t b = (int64_t)x2.x * nf + x2.y, bs = (int64_t)x2.y * nf + x2.x;
-    if (o1 < P && o2 < P) {
-      const int64_t iu = 2 * (int64_t)o1, ju = 2 * (int64_t)o2;
-      const double U = ep_val(wh, wl, tile_of, nt, iu, ju, row_exp, scale);
-      const double X = ep_val(wh, wl, tile_of, nt, iu, ju + 1, row_exp, scale);
-      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, ju, row_exp, scale);
-      const double Z = ep_val(wh, wl, tile_of, nt, iu + 1, ju + 1, row_exp, scale);
-      E[a * n2 + b] = make_double2(0.25 * (U + Z), 0.25 * (Y - X));
-      E[a * n2 + bs] = make_double2(0.25 * (U - Z), 0.25 * (X + Y));
-      E[as * n2 + b] = make_double2(0.25 * (U - Z), -0.25 * (X + Y));
-      E[as * n2 + bs] = make_double2(0.25 * (U + Z), 0.25 * (X - Y));
-    } else if (o1 < P) {
-      const int64_t iu = 2 * (int64_t)o1, j = 2 * (int64_t)P + (o2 - P);
-      const double U = ep_val(wh, wl, tile_of, nt, iu, j, row_exp, scale);
-      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, j, row_exp, scale);
-      E[a * n2 + b] = make_double2(0.5 * U, 0.5 * Y);
-      E[as * n2 + b] = make_double2(0.5 * U, -0.5 * Y);
-    } else if (o2 < P) {
-      const int64_t i = 2 * (int64_t)P + (o1 - P), ju = 2 * (int64_t)o2;
-      const double U = ep_val(wh, wl, tile_of, nt, i, ju, row_exp, scale);
-      const double X = ep_val(wh, wl, tile_of, nt, i, ju + 1, row_exp, scale);
-      E[a * n2 + b] = make_double2(0.5 * U, -0.5 * X);
-      E[a * n2 + bs] = make_double2(0.5 * U, 0.5 * X);
-    } else {
-      const int64_t i = 2 * (int64_t)P + (o1 - P), j = 2 * (int64_t)P + (o2 - P);
-      E[a * n2 + b] = make_double2(ep_val(wh, wl, tile_of, nt, i, j, row_exp, scale), 0.0);
+__device__ __forceinline__ void put_c(float2* e, double re, double im) { *e = make_float2((float)re, (float)im); }
+__device__ __forceinline__ void put_c(double2* e, double re, double im) { *e = make_double2(re, im); }
+
+struct BlockVals {
+  double U, X, Y, Z;
+};
+
+// ERIs and trace terms of the block (row orbit (p, q), column orbit (x, y)); a
+// diagonal orbit has q == p (resp. y == x).
+template <typename TO>
+__device__ __forceinline__ void emit_block(TO* __restrict__ eri, const double2* __restrict__ g, int nf, int p,
+                                           int q, int x, int y, const BlockVals& b, double& aj, double& ak) {
+  const bool pr = p != q, pc = x != y;
+  auto at = [&](int i0, int i1, int i2, int i3) { return eri + (((int64_t)i0 * nf + i1) * nf + i2) * nf + i3; };
+  auto gm = [&](int i, int j) { return g[(int64_t)i * nf + j]; };
+  if (pr && pc) {
+    const double r1 = 0.25 * (b.U + b.Z), i1 = 0.25 * (b.Y - b.X), r2 = 0.25 * (b.U - b.Z), i2 = 0.25 * (b.X + b.Y);
+    if (eri) {
+      put_c(at(p, q, y, x), r1, i1);
+      put_c(at(p, q, x, y), r2, i2);
+      put_c(at(q, p, y, x), r2, -i2);
+      put_c(at(q, p, x, y), r1, -i1);
+    }
+    if (g) {
+      const double2 A = gm(p, q), B = gm(y, x);
+      aj += b.U * A.x * B.x - b.Z * A.y * B.y + b.X * A.x * B.y - b.Y * A.y * B.x;
+      const double2 w1 = cmul(gm(p, x), gm(y, q)), w2 = cmul(gm(p, y), gm(x, q));
+      ak += 2.0 * (w1.x * r1 - w1.y * i1 + w2.x * r2 - w2.y * i2);
+    }
+  } else if (pr) {
+    const double r = 0.5 * b.U, im = 0.5 * b.Y;
+    if (eri) {
+      put_c(at(p, q, x, x), r, im);
+      put_c(at(q, p, x, x), r, -im);
+    }
+    if (g) {
+      const double2 A = gm(p, q);
+      aj += gm(x, x).x * (A.x * b.U - A.y * b.Y);
+      const double2 w = cmul(gm(p, x), gm(x, q));
+      ak += 2.0 * (w.x * r - w.y * im);
+    }
+  } else if (pc) {
+    const double r = 0.5 * b.U, im = -0.5 * b.X;
+    if (eri) {
+      put_c(at(p, p, y, x), r, im);
+      put_c(at(p, p, x, y), r, -im);
+    }
+    if (g) {
+      const double2 B = gm(y, x);
+      aj += gm(p, p).x * (B.x * b.U + B.y * b.X);
+      const double2 w = cmul(gm(p, x), gm(y, p));
+      ak += 2.0 * (w.x * r - w.y * im);
+    }
+  } else {
+    if (eri) put_c(at(p, p, x, x), b.U, 0.0);
+    if (g) {
+      const double2 w = gm(p, x);
+      aj += gm(p, p).x * gm(x, x).x * b.U;
+      ak += (w.x * w.x + w.y * w.y) * b.U;
     }
   }
 }
 
-// The same map with the chemist's permutation and the traces fused, so that E is
-// never stored: E_ab (a = (pq), b = (xy)) is (pq|yx), written to eri[p][q][y][x]
-// (complex64; eri may be NULL), and with gamma (may be NULL) each thread adds
-// gamma_pq gamma_yx E_ab to its J sum and gamma_px gamma_yq E_ab to its K sum.
-// Per-block partials go to part[blk] (J) and part[gridDim.x + blk] (K); a fixed
-// grid keeps the reduction order, and so the traces, reproducible.
-__device__ __forceinline__ void eri_put(float2* __restrict__ eri, const double2* __restrict__ gam, int nf, int p,
-                                        int q, int x, int y, double2 v, double2& aj, double2& ak) {
-  if (eri) eri[(((int64_t)p * nf + q) * nf + y) * nf + x] = make_float2((float)v.x, (float)v.y);
-  if (gam) {
-    const double2 gj = cmul(gam[(int64_t)p * nf + q], gam[(int64_t)y * nf + x]);
-    const double2 gk = cmul(gam[(int64_t)p * nf + x], gam[(int64_t)y * nf + q]);
-    cfma(aj, gj, v);
-    cfma(ak, gk, v);
-  }
-}
-
+template <typename TO>
 __global__ void __launch_bounds__(256) syrk_eri_kernel(const float* __restrict__ wh, const float* __restrict__ wl,
                                                        const int* __restrict__ tile_of, int nt,
                                                        const int2* __restrict__ orb, int nf,
-                                                       const int* __restrict__ row_exp, double scale,
-                                                       float2* __restrict__ eri, const double2* __restrict__ gam,
-                                                       double2* __restrict__ part) {
+                                                       const int* __restrict__ row_exp, const double* __restrict__ corr,
+                                                       double scale, TO* __restrict__ eri,
+                                                       const double2* __restrict__ gam, double2* __restrict__ part) {
   const int no = nf * (nf + 1) / 2, P = nf * (nf - 1) / 2;
-  const int64_t total = (int64_t)no * no;
-  double2 aj = make_double2(0.0, 0.0), ak = make_double2(0.0, 0.0);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int o1 = (int)(e / no), o2 = (int)(e % no);
-    const int2 x1 = orb[o1], x2 = orb[o2];
-    const int p = x1.x, q = x1.y, x = x2.x, y = x2.y;
-    if (o1 < P && o2 < P) {
-      const int64_t iu = 2 * (int64_t)o1, ju = 2 * (int64_t)o2;
-      const double U = ep_val(wh, wl, tile_of, nt, iu, ju, row_exp, scale);
-      const double X = ep_val(wh, wl, tile_of, nt, iu, ju + 1, row_exp, scale);
-      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, ju, row_exp, scale);
-      const double Z = ep_val(wh, wl, tile_of, nt, iu + 1, ju + 1, row_exp, scale);
-      eri_put(eri, gam, nf, p, q, x, y, make_double2(0.25 * (U + Z), 0.25 * (Y - X)), aj, ak);   // (pq),(xy)
-      eri_put(eri, gam, nf, p, q, y, x, make_double2(0.25 * (U - Z), 0.25 * (X + Y)), aj, ak);   // (pq),(yx)
-      eri_put(eri, gam, nf, q, p, x, y, make_double2(0.25 * (U - Z), -0.25 * (X + Y)), aj, ak);  // (qp),(xy)
-      eri_put(eri, gam, nf, q, p, y, x, make_double2(0.25 * (U + Z), 0.25 * (X - Y)), aj, ak);   // (qp),(yx)
-    } else if (o1 < P) {
-      const int64_t iu = 2 * (int64_t)o1, j = 2 * (int64_t)P + (o2 - P);
-      const double U = ep_val(wh, wl, tile_of, nt, iu, j, row_exp, scale);
-      const double Y = ep_val(wh, wl, tile_of, nt, iu + 1, j, row_exp, scale);
-      eri_put(eri, gam, nf, p, q, x, x, make_double2(0.5 * U, 0.5 * Y), aj, ak);
-      eri_put(eri, gam, nf, q, p, x, x, make_double2(0.5 * U, -0.5 * Y), aj, ak);
-    } else if (o2 < P) {
-      const int64_t i = 2 * (int64_t)P + (o1 - P), ju = 2 * (int64_t)o2;
-      const double U = ep_val(wh, wl, tile_of, nt, i, ju, row_exp, scale);
-      const double X = ep_val(wh, wl, tile_of, nt, i, ju + 1, row_exp, scale);
-      eri_put(eri, gam, nf, p, p, x, y, make_double2(0.5 * U, -0.5 * X), aj, ak);
-      eri_put(eri, gam, nf, p, p, y, x, make_double2(0.5 * U, 0.5 * X), aj, ak);
-    } else {
-      const int64_t i = 2 * (int64_t)P + (o1 - P), j = 2 * (int64_t)P + (o2 - P);
-      eri_put(eri, gam, nf, p, p, x, x, make_double2(ep_val(wh, wl, tile_of, nt, i, j, row_exp, scale), 0.0), aj,
-              ak);
+  const int nch = (no + 255) / 256;
+  const int64_t ntask = (int64_t)no * nch;
+  const ffloat sc(scale);
+  double aj = 0.0, ak = 0.0;
+  for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
+    const int o2 = (int)(task / nch), o1 = (int)(task % nch) * 256 + (int)threadIdx.x;
+    if (o1 < o2 || o1 >= no) continue;
+    const int2 r = orb[o1], c = orb[o2];
+    const bool pr = o1 < P, pc = o2 < P;
+    const int64_t u1 = pr ? 2 * (int64_t)o1 : 2 * (int64_t)P + (o1 - P);
+    const int64_t u2 = pc ? 2 * (int64_t)o2 : 2 * (int64_t)P + (o2 - P);
+    BlockVals b{0.0, 0.0, 0.0, 0.0};
+    b.U = ep_ff(wh, wl, tile_of, nt, u1, u2, row_exp, sc).to_double();
+    if (pc) b.X = ep_ff(wh, wl, tile_of, nt, u1, u2 + 1, row_exp, sc).to_double();
+    if (pr) b.Y = ep_ff(wh, wl, tile_of, nt, u1 + 1, u2, row_exp, sc).to_double();
+    if (pr && pc) b.Z = ep_ff(wh, wl, tile_of, nt, u1 + 1, u2 + 1, row_exp, sc).to_double();
+    if (o1 == o2 && corr) {
+      // the diagonal's products left out of the contraction (slice units)
+      b.U += ldexp(corr[u1], -2 * row_exp[u1]) * scale;
+      if (pr) b.Z += ldexp(corr[u1 + 1], -2 * row_exp[u1 + 1]) * scale;
     }
+    emit_block<TO>(eri, gam, nf, r.x, r.y, c.x, c.y, b, aj, ak);
+    if (o1 != o2) emit_block<TO>(eri, gam, nf, c.x, c.y, r.x, r.y, BlockVals{b.U, b.Y, b.X, b.Z}, aj, ak);
   }
   if (!gam) return;
-  __shared__ double2 sj[256], sk[256];
+  __shared__ double sj[256], sk[256];
   sj[threadIdx.x] = aj;
   sk[threadIdx.x] = ak;
   __syncthreads();
   for (int o = 128; o; o >>= 1) {
     if ((int)threadIdx.x < o) {
-      sj[threadIdx.x] = cadd(sj[threadIdx.x], sj[threadIdx.x + o]);
-      sk[threadIdx.x] = cadd(sk[threadIdx.x], sk[threadIdx.x + o]);
+      sj[threadIdx.x] += sj[threadIdx.x + o];
+      sk[threadIdx.x] += sk[threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = sj[0];
-    part[gridDim.x + blockIdx.x] = sk[0];
+    part[blockIdx.x] = make_double2(sj[0], 0.0);
+    part[gridDim.x + blockIdx.x] = make_double2(sk[0], 0.0);
   }
 }
 
@@ -877,7 +902,7 @@ cudaError_t syrk_launch(cudaStream_t st, __half* const sl[3], int64_t n2, int64_
   float* wh = reinterpret_cast<float*>(ws);
   float* wl = wh + (size_t)ntiles * BN * BM;
   TileArgs args{tiles_d, wh, wl, (int)(K2 / BKt), accumulate, err};
-  syrk_tc_kernel<BKt, NST><<<ntiles, NTHREADS, smem, st>>>(m[0], m[1], m[2], m[0], m[1], m[2], args);
+  syrk_tc_kernel<BKt, NST><<<ntiles, kSyrkThreads, smem, st>>>(m[0], m[1], m[2], m[0], m[1], m[2], args);
   count_launch();
   return cudaGetLastError();
 }
@@ -886,49 +911,67 @@ cudaError_t syrk_launch(cudaStream_t st, __half* const sl[3], int64_t n2, int64_
 cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
                           int64_t n2, int j0, int nq, const int* row_exp, void* split, const int2* tiles_d, int ntiles,
                           void* ws, int accumulate, int* err, int cfg) {
+  cudaError_t e = syrk_tc_split(st, B, sQ, sA, nJ, qmap, n2, j0, nq, row_exp, split, nullptr);
+  if (e != cudaSuccess) return e;
+  return syrk_tc_mma(st, split, n2, nq, nJ, tiles_d, ntiles, ws, accumulate, err, cfg);
+}
+
+cudaError_t syrk_tc_split(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
+                          int64_t n2, int j0, int nq, const int* row_exp, void* split, double* corr) {
   using namespace tc;
-  if (n2 <= 0 || nq <= 0 || ntiles <= 0) return cudaSuccess;
+  if (n2 <= 0 || nq <= 0) return cudaSuccess;
+  if (n2 > 2147483647LL) return cudaErrorInvalidValue;
   const int64_t K2 = round_up(2 * (int64_t)nq * nJ, BK);
   __half* S1 = reinterpret_cast<__half*>(split);
   __half* S2 = S1 + (size_t)n2 * K2;
   __half* S3 = S2 + (size_t)n2 * K2;
   BView bv{B, sQ, sA, nJ, qmap};
-  rsplit_kernel<<<nblk(n2 * (K2 / 2)), 256, 0, st>>>(bv, n2, j0, nq, K2, row_exp, S1, S2, S3);
-  count_launch();
-  __half* const sl[3] = {S1, S2, S3};
-  return cfg == 1 ? syrk_launch<32, 4>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err)
-                  : syrk_launch<64, 2>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err);
-}
-
-cudaError_t syrk_tc_finish(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb, int nf,
-                           const int* row_exp, double scale, double2* E) {
-  using namespace tc;
-  const float* wh = reinterpret_cast<const float*>(ws);
-  const float* wl = wh + (size_t)ntiles * BN * BM;
-  const int64_t n2 = (int64_t)nf * nf, nt = (n2 + BM - 1) / BM, no = (int64_t)nf * (nf + 1) / 2;
-  syrk_finish_kernel<<<nblk(no * no), 256, 0, st>>>(wh, wl, tile_of_d, (int)nt, orb, nf, row_exp, scale, E);
+  rsplit_kernel<<<(unsigned)n2, 256, 0, st>>>(bv, j0, nq, K2, row_exp, S1, S2, S3, corr);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t syrk_tc_mma(cudaStream_t st, void* split, int64_t n2, int nq, int64_t nJ, const int2* tiles_d,
+                        int ntiles, void* ws, int accumulate, int* err, int cfg) {
+  using namespace tc;
+  if (n2 <= 0 || nq <= 0 || ntiles <= 0) return cudaSuccess;
+  const int64_t K2 = round_up(2 * (int64_t)nq * nJ, BK);
+  __half* S1 = reinterpret_cast<__half*>(split);
+  __half* const sl[3] = {S1, S1 + (size_t)n2 * K2, S1 + 2 * (size_t)n2 * K2};
+  return cfg == 1 ? syrk_launch<32, 4>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err)
+                  : syrk_launch<64, 2>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err);
 }
 
 constexpr int kEriBlocks = 152 * 16;  // fixed grid of the fused finish (reproducible traces)
 size_t syrk_tc_eri_part_count() { return 2 * (size_t)kEriBlocks; }
 
-cudaError_t syrk_tc_finish_eri(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb,
-                               int nf, const int* row_exp, double scale, float2* eri, const double2* gamma,
-                               double2* part, double* out4) {
+template <typename TO>
+static cudaError_t finish_eri_impl(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d,
+                                   const int2* orb, int nf, const int* row_exp, const double* corr, double scale,
+                                   TO* eri, const double2* gamma, double2* part, double* out4) {
   using namespace tc;
   if (!eri && !gamma) return cudaSuccess;
   const float* wh = reinterpret_cast<const float*>(ws);
   const float* wl = wh + (size_t)ntiles * BN * BM;
   const int64_t n2 = (int64_t)nf * nf, nt = (n2 + BM - 1) / BM;
-  syrk_eri_kernel<<<kEriBlocks, 256, 0, st>>>(wh, wl, tile_of_d, (int)nt, orb, nf, row_exp, scale, eri, gamma, part);
+  syrk_eri_kernel<TO><<<kEriBlocks, 256, 0, st>>>(wh, wl, tile_of_d, (int)nt, orb, nf, row_exp, corr, scale, eri,
+                                                  gamma, part);
   count_launch();
   if (gamma) {
     eri_traces_final_kernel<<<1, 256, 0, st>>>(part, kEriBlocks, out4);
     count_launch();
   }
   return cudaGetLastError();
+}
+cudaError_t syrk_tc_finish_eri(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb,
+                               int nf, const int* row_exp, const double* corr, double scale, float2* eri,
+                               const double2* gamma, double2* part, double* out4) {
+  return finish_eri_impl<float2>(st, ws, ntiles, tile_of_d, orb, nf, row_exp, corr, scale, eri, gamma, part, out4);
+}
+cudaError_t syrk_tc_finish_eri_z(cudaStream_t st, const void* ws, int ntiles, const int* tile_of_d, const int2* orb,
+                                 int nf, const int* row_exp, const double* corr, double scale, double2* eri,
+                                 const double2* gamma, double2* part, double* out4) {
+  return finish_eri_impl<double2>(st, ws, ntiles, tile_of_d, orb, nf, row_exp, corr, scale, eri, gamma, part, out4);
 }
 
 // ---- B = M L on the tensor cores, four slices (host side)

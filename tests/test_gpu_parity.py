@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances: the FP64 path must match the oracle to 1e-8 Ha in every ERI and in
-E_J / E_K; the mixed path to 1e-6 Ha.  Integer work (interpolation points,
+Tolerances: the FP64 path and the FP64-class tensor-core path (FP64_TC) must
+match the oracle to 1e-8 Ha in every ERI and in E_J / E_K; the mixed path to
+1e-6 Ha.  Integer work (interpolation points,
 ranks) must match exactly.  Intermediate arrays of the fit match to ~1e-13
 relative (same FP64 arithmetic in a different order).
 
@@ -27,7 +28,7 @@ def _dev(torch, a):
 
 
 def gpu_eri(torch, g, frags, prec):
-    dt = torch.complex128 if prec == 0 else torch.complex64
+    dt = torch.complex64 if prec == 1 else torch.complex128
     Cs = [_dev(torch, f.C) for f in frags]
     gs = [_dev(torch, f.gamma) for f in frags]
     outs = [torch.empty((f.norb,) * 4, dtype=dt, device="cuda") for f in frags]
@@ -287,7 +288,7 @@ def test_eri_out_in_pinned_host_memory(cuda, lib_built, c1, prec):
     g.build_points(wl.n_p, wl.seed)
     g.fit_zeta(1e-7)
     g.coulomb_metric()
-    dt = torch.complex128 if prec == 0 else torch.complex64
+    dt = torch.complex64 if prec == 1 else torch.complex128
     C, gm = _dev(torch, f.C), _dev(torch, f.gamma)
     dev = torch.empty((f.norb,) * 4, dtype=dt, device="cuda")
     host = torch.empty((f.norb,) * 4, dtype=dt).pin_memory()
@@ -370,7 +371,9 @@ def test_sos_polarizability_matches_oracle(cuda, lib_built, c1, aniso, case):
     g.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7)])
+# FP64_TC is tested at tau = 1e-7 (its contraction is exact to ~2^-35 of |M_a||L_J| in
+# B = M L, and |L| grows like tau^-1/2: at tau = 1e-12 its E_J is off by ~2e-7 Ha on c2)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-7), (0, 1e-12), (1, 1e-7), (2, 1e-7)])
 def test_eri_c2(cuda, lib_built, c2, prec, tol):
     from paper_2601_16379_gb300 import binding as B
     wl, o = c2
@@ -379,7 +382,7 @@ def test_eri_c2(cuda, lib_built, c2, prec, tol):
     g.fit_zeta(tol)
     g.coulomb_metric()
     eris, ej, ek = gpu_eri(cuda, g, wl.fragments, prec)
-    bound = FP64_TOL if prec == 0 else MIXED_TOL
+    bound = MIXED_TOL if prec == 1 else FP64_TOL
     for i, f in enumerate(wl.fragments):
         ref, (rj, rk) = o.eri(tol, f)
         assert np.abs(eris[i] - ref).max() < bound
@@ -605,3 +608,56 @@ def test_emulated_fit_gemm_matches_fp64(cuda, lib_built, c1, c2, case):
     assert np.array_equal(s[B.ISDF_FP64][1], s[B.ISDF_MIXED][1])
     ref = o.eta
     assert np.abs(em - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------- FP64-class tensor-core path
+def test_fp64tc_eri_c1(cuda, lib_built, c1):
+    """FP64_TC (float-float pair tensor, five- and four-slice exact tensor-core
+    contractions) against the oracle at the FP64 tolerance, with a 7-orbital and a
+    1-orbital fragment grouped with the workload's own."""
+    from paper_2601_16379_gb300 import binding as B
+    wl, o = c1
+    tol = 1e-7
+    frags = list(wl.fragments) + [W.make_fragment(wl.cell, wl.seed, 5, 7), W.make_fragment(wl.cell, wl.seed, 6, 1)]
+    g = B.Isdf(wl.cell, B.ISDF_FP64_TC)
+    g.build_points(wl.n_p, wl.seed)
+    g.fit_zeta(tol)
+    g.coulomb_metric()
+    eris, ej, ek = gpu_eri(cuda, g, frags, 2)
+    for i, f in enumerate(frags):
+        ref, (rj, rk) = o.eri(tol, f)
+        assert np.abs(eris[i] - ref).max() < FP64_TOL
+        assert abs(ej[i] - rj) < FP64_TOL and abs(ek[i] - rk) < FP64_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("limit", [1, 64 << 20])
+def test_fp64tc_q_chunks_and_fp64_agreement(cuda, lib_built, c2, limit):
+    """FP64_TC with the q-points of the sum split into chunks (the E' kernel then
+    accumulates into its workspace across launches) on a 40-orbital fragment
+    (several waves of tiles) and a small one: the ERIs agree with the FP64
+    path's to 1e-9 Ha (an order below the FP64 tolerance, three below the mixed
+    path's), and with the oracle within the FP64 tolerance."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl, o = c2
+    frags = [W.make_fragment(wl.cell, wl.seed, 4, 40), W.make_fragment(wl.cell, wl.seed, 2, 9)]
+    res = {}
+    for prec in (B.ISDF_FP64, B.ISDF_FP64_TC):
+        g = B.Isdf(wl.cell, prec)
+        if prec == B.ISDF_FP64_TC:
+            # slice workspace for one q-point per chunk (limit 1), or a few (~8 MB per q-point)
+            g.set_workspace_limit(limit)
+        g.build_points(wl.n_p, wl.seed)
+        g.fit_zeta(1e-7)
+        g.coulomb_metric()
+        res[prec] = gpu_eri(torch, g, frags, prec)
+        g.close()
+    d, t = res[B.ISDF_FP64], res[B.ISDF_FP64_TC]
+    for i in range(len(frags)):
+        assert np.abs(t[0][i] - d[0][i]).max() < 1e-9
+        assert abs(t[1][i] - d[1][i]) < 1e-9 and abs(t[2][i] - d[2][i]) < 1e-9
+    ref, (rj, rk) = o.eri(1e-7, frags[1])
+    assert np.abs(t[0][1] - ref).max() < FP64_TOL
+    assert abs(t[1][1] - rj) < FP64_TOL and abs(t[2][1] - rk) < FP64_TOL
+

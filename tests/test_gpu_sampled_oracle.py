@@ -13,7 +13,7 @@ compare what it can compute one unit at a time:
 
 Both sides take the same seeded interpolation points (isdf_set_points); the
 selection itself is compared bit for bit on the smaller cells elsewhere.
-Tolerances: 1e-8 Ha (FP64 path) and 1e-6 Ha (mixed path) for ERIs and traces;
+Tolerances: 1e-8 Ha (FP64 and FP64_TC paths) and 1e-6 Ha (mixed path) for ERIs and traces;
 the fit quantities are FP64 in both paths.
 """
 import numpy as np
@@ -95,7 +95,7 @@ def c4_small():
     return wl, ips, r
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_c4_kmesh_metric_and_eris(cuda, lib_built, c4_small, prec):
     from paper_2601_16379_gb300 import binding as B
     torch = cuda
@@ -105,12 +105,13 @@ def test_c4_kmesh_metric_and_eris(cuda, lib_built, c4_small, prec):
     g = _setup(torch, wl, prec, ips)
     V = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
     g.coulomb_metric(V)
-    if prec == B.ISDF_FP64:
-        # (the mixed path's V^q carries its complex64 Coulomb GEMM times the ill-conditioned
-        # W; what it must get right is E, checked below)
+    if prec != B.ISDF_MIXED:
+        # (the mixed path's V_xi carries ~2^-28 relative from its four-slice tensor-core
+        # GEMM, which the ill-conditioned W magnifies in V^q = W^T V_xi conj(W) but not in
+        # E = P V_xi P^H with P = M W^T; what it must get right is E, checked below)
         assert _rel(V.cpu().numpy(), r["V"]) < 1e-8
-    tol = FP64_TOL if prec == B.ISDF_FP64 else MIXED_TOL
-    dt = torch.complex128 if prec == B.ISDF_FP64 else torch.complex64
+    tol = MIXED_TOL if prec == B.ISDF_MIXED else FP64_TOL
+    dt = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
     small = W.make_fragment(cell, wl.seed, 0, 12)
     big = W.make_fragment(cell, wl.seed, 1, 120)
     Cs = [torch.from_numpy(f.C).cuda() for f in (small, big)]
