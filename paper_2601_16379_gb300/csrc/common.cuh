@@ -223,6 +223,7 @@ cudaError_t syrk4_tc_split(cudaStream_t st, const ffcomplex* B, int64_t sQ, int6
                            int j0, int nq, const int* row_exp, void* split, double* corr);
 cudaError_t syrk4_tc_mma(cudaStream_t st, void* split, int64_t n2, int nq, int64_t nJ, const int2* tiles_d,
                          int ntiles, void* ws, int accumulate, int* err);
+int mlgemm5_tc_nj_pad(int nj);  // padded complex columns of B (multiple of 96)
 int mlgemm5_tc_kp(int rp);
 bool mlgemm5_tc_supported(int rp);
 size_t mlgemm5_tc_lslice_bytes(int nk, int rp, int nj);

@@ -1019,7 +1019,8 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     int* lexp = nullptr;
     if (tc_ml) {
       lsl = h->ensure_evict("frag_Lsl", tc64 ? mlgemm5_tc_lslice_bytes(nk, rp, nj) : mlgemm_tc_lslice_bytes(nk, rp, nj));
-      lexp = (int*)h->ensure_evict("frag_Lexp", sizeof(int) * (size_t)nk * mlgemm_tc_nj_pad(nj));
+      lexp = (int*)h->ensure_evict("frag_Lexp",
+                                   sizeof(int) * (size_t)nk * (tc64 ? mlgemm5_tc_nj_pad(nj) : mlgemm_tc_nj_pad(nj)));
       if (!lsl || !lexp) return fail(h, ISDF_ERR_OOM, "device allocation of the slices of L failed");
       if (tc64)
         CK(mlgemm5_tc_prepare(h->st, Lq, swd, nk, np, permPi, rankPi, rp, nj, lsl, lexp));

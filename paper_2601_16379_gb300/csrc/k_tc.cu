@@ -540,10 +540,12 @@ __global__ void __launch_bounds__(256) eri_traces_final_kernel(const double2* __
 //
 // Only the structural nonzeros of L^q enter (see the top of the file): the
 // contraction runs over c < r_q with M^q's column perm_q[c] and L^q's row
-// perm_q[c], and the output has n_J columns.  Real form: A' rows
-// P_a = (Re M_a,perm(c), Im M_a,perm(c))_c and Q_a = interleaved(-i M_a,perm(c)),
-// B' rows R_J = (Re L_perm(c)J, -Im L_perm(c)J)_c, so (A' R_J)[P_a] = Re B_aJ and
-// (A' R_J)[Q_a] = Im B_aJ.  M rows are scaled by 2^e_a (largest gathered
+// perm_q[c], and the output has n_J columns.  Real form: one A' row per row of M,
+// P_a = (Re M_a,perm(c), Im M_a,perm(c))_c, and two B' rows per column of L,
+// R_J = (Re L_perm(c)J, -Im L_perm(c)J)_c and I_J = (Im L_perm(c)J, Re L_perm(c)J)_c,
+// so P_a.R_J = Re B_aJ and P_a.I_J = Im B_aJ (the complex embedding sits on the
+// small operand; the slices of M are written and streamed once).  M rows are
+// scaled by 2^e_a (largest gathered
 // component over the q of the sum in [64, 128)), L columns by 2^f_qJ per q; both
 // are cut into four integer slices v = s1 + s2/128 + s3/128^2 + s4/128^3
 // (28 bits: B = M W^T L_xi carries the cancellation of the ill-conditioned W,
@@ -556,7 +558,8 @@ __global__ void __launch_bounds__(256) eri_traces_final_kernel(const double2* __
 // accumulation is exact; the epilogue forms g0 + g1/2^7 + g2/2^14 + g3/2^21
 // once and rescales.
 constexpr int MSL = 4;                                     // slices per operand
-constexpr int MBN = 96;                                    // output columns per tile (N of the MMA)
+constexpr int MBN = 96;                                    // B' rows per tile (N of the MMA)
+constexpr int MBJ = MBN / 2;                               // complex columns of B per tile
 constexpr int MB_BYTES = MBN * BK * 2;                     // 12 KB per slice
 constexpr int MSTAGE_BYTES = MSL * (A_BYTES + MB_BYTES);   // 112 KB
 constexpr int kMlMaxK = 640;                               // K' bound for exact accumulation
@@ -566,7 +569,7 @@ struct MlArgs {
   float2* out;          // B: element (a, J) of sum position j = j0 + ql at out[j sq + a nj + J]
   const int* qmap;      // q of each sum position
   const int* row_exp;   // e_a, [n2]
-  const int* col_exp;   // f_qJ, [Nk][nj_pad] indexed by q
+  const int* col_exp;   // f_qJ, [Nk][nj_pad] indexed by q (nj_pad: complex columns, multiple of MBJ)
   int64_t sq;           // q stride of out
   int n2, nj, nj_pad, j0, nkb;
   int* err;
@@ -589,7 +592,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the output-column tiles of one row block are adjacent in launch order, so
   // they run together and share the row block's slices through L2
-  const int ntj = args.nj_pad / MBN;
+  const int ntj = args.nj_pad / MBJ;
   const int ti = blockIdx.x / ntj, tj = blockIdx.x % ntj, ql = blockIdx.y;
   const int pos = args.j0 + ql;                      // position in the sum (storage of B)
   const int slot = args.qmap ? args.qmap[pos] : pos;  // its q (slices and exponents of L)
@@ -619,7 +622,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       const CUtensorMap* ma[MSL] = {&mA1, &mA2, &mA3, &mA4};
       const CUtensorMap* mb[MSL] = {&mB1, &mB2, &mB3, &mB4};
-      const int arow = ql * 2 * args.n2 + ti * BM, brow = slot * args.nj_pad + tj * MBN;
+      const int arow = ql * args.n2 + ti * BM, brow = slot * 2 * args.nj_pad + tj * MBN;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
         if (!mbar_wait(&empty[s], (r & 1) ^ 1, s_err, args.err, 11)) break;
@@ -671,20 +674,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (ok) umma_commit(accf);
     }
   } else {
-    // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4); rows P_a / Q_a are lanes 2i / 2i+1
+    // epilogue: warps 2..5 -> TMEM lane quarter (warp % 4); lane r is row a of M, TMEM
+    // column n is B' row n of the tile: complex column Jl = n / 2, part n % 2 (Re, Im)
     const int q = warp & 3;
-    const int r = q * 32 + lane;            // row of the tile
-    const int64_t R = (int64_t)ti * BM + r;  // row of A'
-    const int al = r >> 1, part = r & 1;
-    const int64_t a = R >> 1;
+    const int r = q * 32 + lane;             // row of the tile
+    const int64_t a = (int64_t)ti * BM + r;  // row of M (of the q-point's block)
     // warp-uniform, so that the .sync.aligned TMEM loads are taken by whole warps
     const bool okw = __all_sync(0xffffffffu, mbar_wait(accf, 0, s_err, args.err, 13));
     tc_fence_after();
-    // the operand stages are idle now: stage the 64 x MBN complex tile for coalesced stores
-    constexpr int kPitch = 2 * MBN + 2;     // floats per staged row (bank-conflict padding)
+    // the operand stages are idle now: stage the 128 x MBJ complex tile for coalesced stores
+    constexpr int kPitch = MBN + 2;     // floats per staged row (bank-conflict padding)
     float* tileS = reinterpret_cast<float*>(smem);
     const int ea = (okw && a < args.n2) ? args.row_exp[a] : 0;
-    const int* fcol = args.col_exp + (int64_t)slot * args.nj_pad + tj * MBN;
+    const int* fcol = args.col_exp + (int64_t)slot * args.nj_pad + tj * MBJ;
 #pragma unroll 1
     for (int cb = 0; cb < MBN / 32; ++cb) {
       uint32_t v0[32] = {}, v1[32] = {}, v2[32] = {}, v3[32] = {};
@@ -700,18 +702,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const float v = __uint_as_float(v0[j]) +
                         (__uint_as_float(v1[j]) * (1.0f / 128.0f) +
                          (__uint_as_float(v2[j]) * (1.0f / 16384.0f) + __uint_as_float(v3[j]) * (1.0f / 2097152.0f)));
-        const int Jl = cb * 32 + j;
-        tileS[al * kPitch + 2 * Jl + part] = ldexpf(v, -(ea + fcol[Jl]));
+        const int n = cb * 32 + j;
+        tileS[r * kPitch + n] = ldexpf(v, -(ea + fcol[n >> 1]));
       }
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     if (okw) {
       const int t = threadIdx.x - 64;
       float2* outq = args.out + (int64_t)pos * args.sq;
-      for (int idx = t; idx < (BM / 2) * MBN; idx += 128) {
-        const int ar = idx / MBN, Jl = idx % MBN;
-        const int64_t aa = (int64_t)ti * (BM / 2) + ar;
-        const int J = tj * MBN + Jl;
+      for (int idx = t; idx < BM * MBJ; idx += 128) {
+        const int ar = idx / MBJ, Jl = idx % MBJ;
+        const int64_t aa = (int64_t)ti * BM + ar;
+        const int J = tj * MBJ + Jl;
         if (aa < args.n2 && J < args.nj)
           outq[aa * args.nj + J] = *reinterpret_cast<const float2*>(tileS + ar * kPitch + 2 * Jl);
       }
@@ -763,8 +765,8 @@ __global__ void mrow_scale_kernel(const float2* __restrict__ M, int64_t sq, int 
 }
 
 // A' slices of M for the sum positions j0..j0+nq-1 (M^q stored by position,
-// q = qmap[j]): block ql holds rows 2a (P_a) and 2a+1 (Q_a) over Kp columns:
-// the gathered columns perm_q[c], c < r_q, zero beyond.
+// q = qmap[j]): block ql holds row a = P_a over Kp columns: the gathered columns
+// perm_q[c], c < r_q, as (re, im) pairs, zero beyond.
 __global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, const int* __restrict__ qmap,
                               const int* __restrict__ perm, const int* __restrict__ rank, int64_t n2, int j0, int nq,
                               int Kp, const int* __restrict__ row_exp, __half* __restrict__ S1,
@@ -777,32 +779,27 @@ __global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, 
     float2 v = make_float2(0.f, 0.f);
     if (c < rank[q]) v = M[(int64_t)(j0 + ql) * sq + a * np + perm[(int64_t)q * np + c]];
     const int ex = row_exp[a];
-    const float pr = ldexpf(v.x, ex), pi = ldexpf(v.y, ex);
-    const float vals[4] = {pr, pi, pi, -pr};
-    __half h1[4], h2[4], h3[4], h4[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) slice4<float>(vals[t], h1[t], h2[t], h3[t], h4[t]);
-    const int64_t rP = (ql * 2 * n2 + 2 * a) * Kp + 2 * c, rQ = rP + Kp;
-    *reinterpret_cast<__half2*>(S1 + rP) = __halves2half2(h1[0], h1[1]);
-    *reinterpret_cast<__half2*>(S2 + rP) = __halves2half2(h2[0], h2[1]);
-    *reinterpret_cast<__half2*>(S3 + rP) = __halves2half2(h3[0], h3[1]);
-    *reinterpret_cast<__half2*>(S4 + rP) = __halves2half2(h4[0], h4[1]);
-    *reinterpret_cast<__half2*>(S1 + rQ) = __halves2half2(h1[2], h1[3]);
-    *reinterpret_cast<__half2*>(S2 + rQ) = __halves2half2(h2[2], h2[3]);
-    *reinterpret_cast<__half2*>(S3 + rQ) = __halves2half2(h3[2], h3[3]);
-    *reinterpret_cast<__half2*>(S4 + rQ) = __halves2half2(h4[2], h4[3]);
+    __half r1, r2, r3, r4, i1, i2, i3, i4;
+    slice4<float>(ldexpf(v.x, ex), r1, r2, r3, r4);
+    slice4<float>(ldexpf(v.y, ex), i1, i2, i3, i4);
+    const int64_t at = (ql * n2 + a) * Kp + 2 * c;
+    *reinterpret_cast<__half2*>(S1 + at) = __halves2half2(r1, i1);
+    *reinterpret_cast<__half2*>(S2 + at) = __halves2half2(r2, i2);
+    *reinterpret_cast<__half2*>(S3 + at) = __halves2half2(r3, i3);
+    *reinterpret_cast<__half2*>(S4 + at) = __halves2half2(r4, i4);
   }
 }
 
-// B' slices of w_q^{1/2} L^q: block (J, q) is the row R_J = (Re L_perm(c)J, -Im L_perm(c)J)_c
-// scaled by 2^f_qJ (largest component in [64, 128)); rows J >= nj, columns
-// c >= r_q and columns beyond 2 r_q are zero.  Layout [q][nj_pad][Kp] per
-// slice; exponents [q][nj_pad].
+// B' slices of w_q^{1/2} L^q: block (row, q), row = 2 J + part, is R_J = (Re L, -Im L)
+// (part 0) or I_J = (Im L, Re L) (part 1) over the gathered rows perm_q(c) of column J,
+// scaled by 2^f_qJ (largest component of the column in [64, 128)); columns J >= nj,
+// c >= r_q and beyond 2 r_q are zero.  Layout [q][2 nj_pad][Kp] per slice;
+// exponents [q][nj_pad].
 __global__ void lslice_kernel(const double2* __restrict__ L, const double* __restrict__ sw, int np,
                               const int* __restrict__ perm, const int* __restrict__ rank, int nj, int nj_pad, int Kp,
                               __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3,
                               __half* __restrict__ S4, int* __restrict__ col_exp) {
-  const int q = blockIdx.y, J = blockIdx.x;
+  const int q = blockIdx.y, J = blockIdx.x >> 1, part = blockIdx.x & 1;
   const double w = sw[q];
   const int r = rank[q];
   const double2* Lq = L + (int64_t)q * np * np;
@@ -816,14 +813,15 @@ __global__ void lslice_kernel(const double2* __restrict__ L, const double* __res
   __shared__ double sm[32];
   m = block_max(m, sm);
   const int ex = (m > 0.0 && isfinite(m)) ? 6 - ilogb(m) : 0;
-  if (threadIdx.x == 0) col_exp[(int64_t)q * nj_pad + J] = ex;
-  const int64_t row = ((int64_t)q * nj_pad + J) * Kp;
+  if (threadIdx.x == 0 && part == 0) col_exp[(int64_t)q * nj_pad + J] = ex;
+  const int64_t row = ((int64_t)q * 2 * nj_pad + blockIdx.x) * Kp;
   for (int c = threadIdx.x; c < Kp / 2; c += blockDim.x) {
     double re = 0.0, im = 0.0;
     if (J < nj && c < r) {
       const double2 v = Lq[(int64_t)pq[c] * np + J];
-      re = ldexp(v.x * w, ex);
-      im = -ldexp(v.y * w, ex);
+      const double lr = ldexp(v.x * w, ex), li = ldexp(v.y * w, ex);
+      re = part ? li : lr;
+      im = part ? lr : -li;
     }
     __half a1, a2, a3, a4, b1, b2, b3, b4;
     slice4<double>(re, a1, a2, a3, a4);
@@ -976,23 +974,23 @@ cudaError_t syrk_tc_finish_eri_z(cudaStream_t st, const void* ws, int ntiles, co
 
 // ---- B = M L on the tensor cores, four slices (host side)
 int mlgemm_tc_kp(int rp) { return (int)tc::round_up(2 * (int64_t)rp, tc::BK); }
-int mlgemm_tc_nj_pad(int nj) { return (int)tc::round_up(nj, tc::MBN); }
+int mlgemm_tc_nj_pad(int nj) { return (int)tc::round_up(nj, tc::MBJ); }
 bool mlgemm_tc_supported(int rp) { return rp > 0 && mlgemm_tc_kp(rp) <= tc::kMlMaxK; }
 size_t mlgemm_tc_lslice_bytes(int nk, int rp, int nj) {
-  return (size_t)tc::MSL * nk * mlgemm_tc_nj_pad(nj) * mlgemm_tc_kp(rp) * sizeof(__half) + 256;
+  return (size_t)tc::MSL * nk * (2 * mlgemm_tc_nj_pad(nj)) * mlgemm_tc_kp(rp) * sizeof(__half) + 256;
 }
 size_t mlgemm_tc_split_bytes(int64_t n2, int rp, int nq) {
-  return (size_t)tc::MSL * nq * (2 * n2) * mlgemm_tc_kp(rp) * sizeof(__half) + 256;
+  return (size_t)tc::MSL * nq * n2 * mlgemm_tc_kp(rp) * sizeof(__half) + 256;
 }
 
 cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, const int* perm,
                               const int* rank, int rp, int nj, void* lsl, int* col_exp) {
   using namespace tc;
   const int Kp = mlgemm_tc_kp(rp), njp = mlgemm_tc_nj_pad(nj);
-  const size_t per = (size_t)nk * njp * Kp;
+  const size_t per = (size_t)nk * 2 * njp * Kp;
   __half* S1 = reinterpret_cast<__half*>(lsl);
-  lslice_kernel<<<dim3(njp, nk), 128, 0, st>>>(L, sw, np, perm, rank, nj, njp, Kp, S1, S1 + per, S1 + 2 * per,
-                                                S1 + 3 * per, col_exp);
+  lslice_kernel<<<dim3(2 * njp, nk), 128, 0, st>>>(L, sw, np, perm, rank, nj, njp, Kp, S1, S1 + per, S1 + 2 * per,
+                                                    S1 + 3 * per, col_exp);
   count_launch();
   return cudaGetLastError();
 }
@@ -1011,7 +1009,7 @@ cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* q
   if (n2 <= 0 || nq <= 0) return cudaSuccess;
   if (!mlgemm_tc_supported(rp)) return cudaErrorInvalidValue;
   const int Kp = mlgemm_tc_kp(rp), njp = mlgemm_tc_nj_pad(nj);
-  const size_t pa = (size_t)nq * (2 * n2) * Kp, pb = (size_t)nk * njp * Kp;
+  const size_t pa = (size_t)nq * n2 * Kp, pb = (size_t)nk * 2 * njp * Kp;
   __half* S1 = reinterpret_cast<__half*>(split);
   msplit_kernel<<<nblk((int64_t)nq * n2 * (Kp / 2)), 256, 0, st>>>(M, sq, np, qmap, perm, rank, n2, j0, nq, Kp,
                                                                    row_exp, S1, S1 + pa, S1 + 2 * pa, S1 + 3 * pa);
@@ -1019,13 +1017,13 @@ cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* q
   const __half* L1 = reinterpret_cast<const __half*>(lsl);
   CUtensorMap mA[MSL], mB[MSL];
   for (int i = 0; i < MSL; ++i)
-    if (!make_map(&mA[i], S1 + i * pa, Kp, (int64_t)nq * 2 * n2, Kp, BM) ||
-        !make_map(&mB[i], L1 + i * pb, Kp, (int64_t)nk * njp, Kp, MBN))
+    if (!make_map(&mA[i], S1 + i * pa, Kp, (int64_t)nq * n2, Kp, BM) ||
+        !make_map(&mB[i], L1 + i * pb, Kp, (int64_t)nk * 2 * njp, Kp, MBN))
       return cudaErrorInvalidValue;
   const size_t smem = (size_t)STAGES * MSTAGE_BYTES + 1024 + 256;
   cudaError_t e = cudaFuncSetAttribute(mlgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int mt = (int)((2 * n2 + BM - 1) / BM), ntj = njp / MBN;
+  const int mt = (int)((n2 + BM - 1) / BM), ntj = njp / MBJ;
   MlArgs args{M, qmap, row_exp, col_exp, sq, (int)n2, nj, njp, j0, Kp / BK, err};
   mlgemm_tc_kernel<<<dim3(mt * ntj, nq), NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mA[3], mB[0], mB[1], mB[2],
                                                                 mB[3], args);

@@ -645,10 +645,11 @@ cudaError_t syrk4_tc_mma(cudaStream_t st, void* split, int64_t n2, int nq, int64
   return cudaGetLastError();
 }
 
+int mlgemm5_tc_nj_pad(int nj) { return (int)tc64::rup(nj, tc64::MBN); }
 int mlgemm5_tc_kp(int rp) { return (int)tc64::rup(2 * (int64_t)rp, tc64::BKt); }
 bool mlgemm5_tc_supported(int rp) { return rp > 0 && mlgemm5_tc_kp(rp) <= tc64::kMl5MaxK; }
 size_t mlgemm5_tc_lslice_bytes(int nk, int rp, int nj) {
-  return (size_t)tc64::NS5 * nk * mlgemm_tc_nj_pad(nj) * mlgemm5_tc_kp(rp) * sizeof(__half) + 256;
+  return (size_t)tc64::NS5 * nk * mlgemm5_tc_nj_pad(nj) * mlgemm5_tc_kp(rp) * sizeof(__half) + 256;
 }
 size_t mlgemm5_tc_split_bytes(int64_t n2, int rp, int nq) {
   return (size_t)tc64::NS5 * nq * (2 * n2) * mlgemm5_tc_kp(rp) * sizeof(__half) + 256;
@@ -656,7 +657,7 @@ size_t mlgemm5_tc_split_bytes(int64_t n2, int rp, int nq) {
 
 cudaError_t mlgemm5_tc_prepare(cudaStream_t st, const double2* L, const double* sw, int nk, int np, const int* perm,
                                const int* rank, int rp, int nj, void* lsl, int* col_exp) {
-  const int Kp = mlgemm5_tc_kp(rp), njp = mlgemm_tc_nj_pad(nj);
+  const int Kp = mlgemm5_tc_kp(rp), njp = mlgemm5_tc_nj_pad(nj);
   if (njp % tc64::MBN != 0) return cudaErrorInvalidValue;
   const size_t per = (size_t)nk * njp * Kp;
   tc64::lslice5_kernel<<<dim3(njp, nk), 128, 0, st>>>(L, sw, np, perm, rank, nj, njp, Kp,
@@ -679,7 +680,7 @@ cudaError_t mlgemm5_tc_chunk(cudaStream_t st, ffcomplex* M, int64_t sq, const in
   using namespace tc64;
   if (n2 <= 0 || nq <= 0) return cudaSuccess;
   if (!mlgemm5_tc_supported(rp)) return cudaErrorInvalidValue;
-  const int Kp = mlgemm5_tc_kp(rp), njp = mlgemm_tc_nj_pad(nj);
+  const int Kp = mlgemm5_tc_kp(rp), njp = mlgemm5_tc_nj_pad(nj);
   const size_t pa = (size_t)nq * (2 * n2) * Kp, pb = (size_t)nk * njp * Kp;
   __half* S = reinterpret_cast<__half*>(split);
   msplit5_kernel<<<nblk((int64_t)nq * n2 * (Kp / 2)), 256, 0, st>>>(M, sq, np, qmap, perm, rank, n2, j0, nq, Kp,
