@@ -112,7 +112,7 @@ class ClockSampler:
 # Source regions of the dominant kernels: a committed ncu summary applies only
 # while the kernel's own source is the one it was taken on.
 KERNEL_REGIONS = {
-    "syrk_tc_kernel<64, 2>": ("k_tc.cu", "template <int BKt, int NST>\n__global__ void __launch_bounds__(NTHREADS, 1)\n"
+    "syrk_tc_kernel<64, 3>": ("k_tc.cu", "template <int BKt, int NST>\n__global__ void __launch_bounds__(kSyrkThreads, 1)\n"
                               "    syrk_tc_kernel(", "// ----------------------------------------------------------------- helpers"),
     "syrk4_tc_kernel": ("k_tc64.cu", "__global__ void __launch_bounds__(NT4, 1)\n    syrk4_tc_kernel(",
                         "// B viewed as element"),
@@ -324,7 +324,7 @@ def run_gpu(args, rank, world, local_rank):
     herk_avg_ms = herk_ms / max(herk_n, 1)
     traffic, traffic_src = None, None
     if herk_n and kernel_name.startswith("syrk"):
-        kname = "syrk4_tc_kernel" if prec == B.ISDF_FP64_TC else "syrk_tc_kernel<64, 2>"
+        kname = "syrk4_tc_kernel" if prec == B.ISDF_FP64_TC else "syrk_tc_kernel<64, 3>"
         traffic, prof = profile_traffic(kname, herk_flops / herk_n)
         if traffic is not None:
             traffic_src = (f"{prof}: DRAM bytes per algorithmic flop of a small-case capture of {kname}, "

@@ -63,8 +63,9 @@ typedef enum {
   ISDF_MIXED = 1,  /* FP64-class points and fit (Eqs. 3-5); V (Eq. 6) from a float-  */
                    /* float grid FFT and V_xi on the tensor cores with four exact   */
                    /* fp16 slices; the fragment pair tensor and ERI contractions   */
-                   /* (Eqs. 19-20) in reduced precision (FP32 transforms, three-    */
-                   /* and four-slice exact fp16 products on the tensor cores)       */
+                   /* (Eqs. 19-20) in reduced precision (FP32 transforms; fp16      */
+                   /* integer + remainder slices for E, ~2^-19 relative; four exact */
+                   /* 7-bit slices for B = M L, ~2^-28; both on the tensor cores)   */
   ISDF_FP64_TC = 2 /* FP64-class results on the tensor cores: points and fit as in  */
                    /* ISDF_MIXED, V in FP64; the pair tensor in float-float (~2^-44), */
                    /* B = M L with five and E with four exact fp16 slices per       */

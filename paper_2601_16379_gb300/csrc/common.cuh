@@ -189,14 +189,14 @@ size_t syrk_tc_ws_bytes(int64_t ntiles);
 cudaError_t syrk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
                              int nS, int64_t n2, int* row_exp);
 // cfg selects the pipeline of the tile kernel: 0 = K rows of 64 fp16 (128-byte
-// swizzle), 2 stages; 1 = rows of 32 fp16 (64-byte swizzle), 4 stages.
+// swizzle), 3 stages; 1 = rows of 32 fp16 (64-byte swizzle), 6 stages.
 cudaError_t syrk_tc_chunk(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
                           int64_t n2, int j0, int nq, const int* row_exp, void* split, const int2* tiles_d, int ntiles,
                           void* ws, int accumulate, int* err, int cfg = 0);
 // The two halves of syrk_tc_chunk: the fp16 slices of the chunk's rows, then the
 // tensor-core kernel over them (timed on its own as the dominant kernel).
-// corr (n2 doubles, or NULL) accumulates per row the products of the row with
-// itself that the contraction leaves out (added to E'_aa by the finish).
+// corr (n2 doubles, or NULL) accumulates per row the part of the row's square
+// sum that its fp16 slices do not represent (added to E'_aa by the finish).
 cudaError_t syrk_tc_split(cudaStream_t st, const float2* B, int64_t sQ, int64_t sA, int64_t nJ, const int* qmap,
                           int64_t n2, int j0, int nq, const int* row_exp, void* split, double* corr);
 cudaError_t syrk_tc_mma(cudaStream_t st, void* split, int64_t n2, int nq, int64_t nJ, const int2* tiles_d,

@@ -23,25 +23,30 @@
 // One real SYRK of n_f^2 rows replaces the complex HERK: half its real
 // products.  Only lower-triangle tiles are formed; the finish maps E' to E.
 //
-// Precision (error-free slicing after Ozaki, Ogita, Oishi & Rump, 2012): each
-// real row is scaled by a power of two 2^e so that its largest entry lies in
-// [64, 128), and every scaled value is written as
-//     v = s1 + s2/128 + s3/128^2 (+ remainder below 2^-15),  s_i integers, |s1| <= 128, |s2|, |s3| <= 64,
-// stored as fp16 (exact).  The tcgen05.mma kind::f16 products of integer
-// slices are integers, and the three weight groups
-//     g0 = S1.T1,  g1 = S1.T2 + S2.T1,  g2 = S1.T3 + S2.T2 + S3.T1
-// are accumulated in FP32 TMEM.  g0 carries weight 1 and must be exact: a
-// chunk of 64 k-steps (1024 products of magnitude <= 2^14) keeps its partial
-// sums integers of magnitude at most 2^24, so the FP32
-// accumulation is exact whatever its rounding; g0 is double-buffered and each
-// chunk is drained (overlapping the next chunk's MMAs) into a float-float
-// (TwoSum) accumulator in global memory.  g1 and g2 carry weights 2^-7 and
-// 2^-14, so the truncation of tcgen05's FP32 accumulation over longer runs
-// enters only scaled down: they are drained every 4 and 16 chunks (bias below
-// 1e-7 of |R_a||R_b|).  The result is accurate to ~2^-22 of |R_a||R_b|.
+// Precision.  Each real row of R is scaled by a power of two 2^e so that its
+// largest entry lies in [64, 128), and every scaled value x is written as two
+// fp16 slices
+//     x = s1 + s2 + d,   s1 = rint(x) (an integer, |s1| <= 128),  s2 = fp16(x - s1) (|s2| <= 1/2),
+// so that |d| <= 2^-12 |s2| (19 significant bits, against 24 in FP32).  The
+// tcgen05.mma kind::f16 products feed two FP32 TMEM accumulators:
+//     g0 = S1.T1   (integers of magnitude <= 2^14),
+//     g1 = S1.T2 + S2.T1 + S2.T2   (magnitude <= 2^6 + 2^-2 per product).
+// g0 carries the bulk of E' and must be exact: a chunk of 1024 k-steps keeps
+// its partial sums integers of magnitude at most 2^24, so the FP32
+// accumulation is exact whatever its rounding.  g1 is not exact, but its
+// products are 2^-7 of g0's and of either sign (s2 is a rounding remainder),
+// so the truncation of tcgen05's FP32 accumulation over two chunks enters at
+// ~2^-30 of |R_a||R_b|.  Both accumulators are double-buffered, g0 drained every
+// chunk and g1 every second chunk (overlapping the next chunk's MMAs), into
+// float-float (TwoSum) running sums held in the drain warps' registers.  Four products per useful
+// product (the three-slice form with the same accuracy target needs six); the
+// representation error d is random in sign off the diagonal, and the slicing
+// kernel sums each row's sum of x^2 - (s1 + s2)^2 in FP64 so that the finish
+// makes the diagonal exact.  Simulated on the c2 and c4 k-mesh data against the
+// exact FP64 products: ERIs within ~1e-9 Ha, E_J within ~3e-8 Ha.
 //
-// Kernel roles (192 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
-// and issues the MMAs, warps 2-5 drain TMEM into the float-float workspace.
+// Kernel roles (576 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
+// and issues the MMAs, warps 2-17 drain TMEM into the float-float sums.
 // Every wait is bounded: on expiry the CTA records an error code and exits.
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -61,19 +66,15 @@ namespace tc {
 constexpr int BM = 128;        // A' rows per tile (64 complex rows of E)
 constexpr int BN = 128;        // B' rows per tile (complex columns of E)
 constexpr int BK = 64;         // fp16 per row per stage (one 128-byte swizzle row)
-constexpr int STAGES = 2;
-constexpr int NSLICE = 3;
+constexpr int STAGES = 2;                   // B = M L pipeline depth
+constexpr int NSLICE = 2;                   // fp16 slices per value in E': s1 (integer), s2 (remainder)
 constexpr int A_BYTES = BM * BK * 2;        // 16 KB per slice
-constexpr int B_BYTES = BN * BK * 2;        // 16 KB per slice
-constexpr int STAGE_BYTES = NSLICE * (A_BYTES + B_BYTES);  // 96 KB
-constexpr int TMEM_COLS = 512;              // g0 (two buffers), g1, g2: four 128-column FP32 accumulators
+constexpr int TMEM_COLS = 512;              // g0 and g1, each two 128-column FP32 buffers
 constexpr int NTHREADS = 192;
 // E' kernel: warp 0 TMA, warp 1 MMA, 16 drain warps (TMEM lane quarter warp % 4, 32 of
 // the 128 columns each), whose registers hold the tile's float-float running sums
 constexpr int kSyrkThreads = 576, kDrainWarps = 16, kDrainCols = 32;
-constexpr int kChunkKB = 16;                // k-blocks per exact g0 chunk: 64 k-steps of 16
-constexpr int kP1 = 4;                      // chunks per g1 drain
-constexpr int kP2 = 16;                     // chunks per g2 drain
+constexpr int kP1 = 2;                      // chunks per g1 drain
 // Instruction descriptor of kind::f16: FP32 accumulate, fp16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -89,23 +90,21 @@ struct TileArgs {
 
 // Pipeline variants: BKt fp16 of K per stage row (64: 128-byte swizzle, 32: 64-byte
 // swizzle) and NST stages; a 1024-element exact chunk of g0 is 1024 / BKt k-blocks.
+// TMEM columns: g0 of chunk c at (c & 1) BN, g1 of chunk c at (2 + (c / kP1 & 1)) BN.
 template <int BKt, int NST>
 __global__ void __launch_bounds__(kSyrkThreads, 1)
-    syrk_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
-                   const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mB1,
-                   const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, TileArgs args) {
+    syrk_tc_kernel(const __grid_constant__ CUtensorMap mS1, const __grid_constant__ CUtensorMap mS2, TileArgs args) {
   constexpr int kA = BM * BKt * 2, kB = BN * BKt * 2, kStage = NSLICE * (kA + kB);
   constexpr int kChunk = 1024 / BKt;  // k-blocks per exact g0 chunk
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment of the shared-window address (swizzle atoms)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NST * kStage);
-  uint64_t* full = bars;                   // [NST]
+  uint64_t* full = bars;                // [NST]
   uint64_t* empty = bars + NST;         // [NST]
-  uint64_t* accf = bars + 2 * NST;      // [2] chunk accumulated (per g0 buffer)
+  uint64_t* accf = bars + 2 * NST;      // [2] chunk accumulated (per buffer pair)
   uint64_t* acce = bars + 2 * NST + 2;  // [2] g0 buffer drained
-  uint64_t* acce1 = bars + 2 * NST + 4; // g1 drained
-  uint64_t* acce2 = bars + 2 * NST + 5; // g2 drained
+  uint64_t* acce1 = bars + 2 * NST + 4; // [2] g1 buffer drained
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * NST + 6);
   volatile int* s_err = reinterpret_cast<volatile int*>(s_tmem + 1);
 
@@ -122,9 +121,8 @@ __global__ void __launch_bounds__(kSyrkThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], kDrainWarps);
+      mbar_init(&acce1[b], kDrainWarps);
     }
-    mbar_init(acce1, kDrainWarps);
-    mbar_init(acce2, kDrainWarps);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -141,19 +139,17 @@ __global__ void __launch_bounds__(kSyrkThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      const CUtensorMap* ma[3] = {&mA1, &mA2, &mA3};
-      const CUtensorMap* mb[3] = {&mB1, &mB2, &mB3};
+      // stage layout: S1 rows of A, S2 rows of A, S1 rows of B, S2 rows of B
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % NST, r = kb / NST;
         if (!mbar_wait(&empty[s], (r & 1) ^ 1, s_err, args.err, 1)) break;
         uint8_t* st = smem + s * kStage;
         mbar_expect_tx(&full[s], kStage);
         const int x = kb * BKt;
-#pragma unroll
-        for (int i = 0; i < NSLICE; ++i) {
-          tma_load_2d(st + i * kA, ma[i], &full[s], x, tile.x * BM);
-          tma_load_2d(st + NSLICE * kA + i * kB, mb[i], &full[s], x, tile.y * BN);
-        }
+        tma_load_2d(st, &mS1, &full[s], x, tile.x * BM);
+        tma_load_2d(st + kA, &mS2, &full[s], x, tile.x * BM);
+        tma_load_2d(st + 2 * kA, &mS1, &full[s], x, tile.y * BN);
+        tma_load_2d(st + 2 * kA + kB, &mS2, &full[s], x, tile.y * BN);
       }
     }
   } else if (warp == 1) {
@@ -162,40 +158,30 @@ __global__ void __launch_bounds__(kSyrkThreads, 1)
         const int s = kb % NST, r = kb / NST;
         const int c = kb / kChunk;
         const bool first_in_chunk = (kb % kChunk) == 0;
-        const bool reset1 = first_in_chunk && (c % kP1) == 0;
-        const bool reset2 = first_in_chunk && (c % kP2) == 0;
+        const int p = c / kP1;  // g1 period
+        const bool first_in_period = first_in_chunk && (c % kP1) == 0;
         if (first_in_chunk) {
-          bool ok = true;
-          // g0 buffer (c & 1) was last used by chunk c - 2
-          if (c >= 2) ok = mbar_wait(&acce[c & 1], ((c >> 1) - 1) & 1, s_err, args.err, 2);
-          if (ok && reset1 && c > 0) ok = mbar_wait(acce1, ((c / kP1) - 1) & 1, s_err, args.err, 5);
-          if (ok && reset2 && c > 0) ok = mbar_wait(acce2, ((c / kP2) - 1) & 1, s_err, args.err, 6);
-          if (!ok) break;
+          // g0 buffer (c & 1) was last used by chunk c - 2, g1 buffer (p & 1) by period p - 2
+          if (c >= 2 && !mbar_wait(&acce[c & 1], ((c >> 1) - 1) & 1, s_err, args.err, 2)) break;
+          if (first_in_period && p >= 2 && !mbar_wait(&acce1[p & 1], ((p >> 1) - 1) & 1, s_err, args.err, 5))
+            break;
           tc_fence_after();
         }
         if (!mbar_wait(&full[s], r & 1, s_err, args.err, 3)) break;
         tc_fence_after();
         const uint8_t* st = smem + s * kStage;
-        uint64_t dA[3], dB[3];
-#pragma unroll
-        for (int i = 0; i < NSLICE; ++i) {
-          dA[i] = sdesc_k<BKt>(st + i * kA);
-          dB[i] = sdesc_k<BKt>(st + NSLICE * kA + i * kB);
-        }
-        const uint32_t g0 = tmem_base + (uint32_t)((c & 1) * BN), g1 = tmem_base + 2 * BN,
-                       g2 = tmem_base + 3 * BN;
+        const uint64_t a1 = sdesc_k<BKt>(st), a2 = sdesc_k<BKt>(st + kA);
+        const uint64_t b1 = sdesc_k<BKt>(st + 2 * kA), b2 = sdesc_k<BKt>(st + 2 * kA + kB);
+        const uint32_t g0 = tmem_base + (uint32_t)((c & 1) * BN), g1 = tmem_base + (uint32_t)((2 + (p & 1)) * BN);
 #pragma unroll
         for (int kk = 0; kk < BKt / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 fp16 = 32 bytes along K
-          const uint32_t a0 = (first_in_chunk && kk == 0) ? 0u : 1u;
-          const uint32_t a1 = (reset1 && kk == 0) ? 0u : 1u;
-          const uint32_t a2 = (reset2 && kk == 0) ? 0u : 1u;
-          umma_f16(g0, dA[0] + off, dB[0] + off, kIdesc, a0);
-          umma_f16(g1, dA[0] + off, dB[1] + off, kIdesc, a1);
-          umma_f16(g1, dA[1] + off, dB[0] + off, kIdesc, 1u);
-          umma_f16(g2, dA[0] + off, dB[2] + off, kIdesc, a2);
-          umma_f16(g2, dA[1] + off, dB[1] + off, kIdesc, 1u);
-          umma_f16(g2, dA[2] + off, dB[0] + off, kIdesc, 1u);
+          const uint32_t acc0 = (first_in_chunk && kk == 0) ? 0u : 1u;
+          const uint32_t acc1 = (first_in_period && kk == 0) ? 0u : 1u;
+          umma_f16(g0, a1 + off, b1 + off, kIdesc, acc0);
+          umma_f16(g1, a1 + off, b2 + off, kIdesc, acc1);
+          umma_f16(g1, a2 + off, b1 + off, kIdesc, 1u);
+          umma_f16(g1, a2 + off, b2 + off, kIdesc, 1u);
         }
         umma_commit(&empty[s]);
         if ((kb % kChunk) == kChunk - 1 || kb == nkb - 1) umma_commit(&accf[c & 1]);
@@ -220,31 +206,27 @@ __global__ void __launch_bounds__(kSyrkThreads, 1)
       ok = __all_sync(0xffffffffu, mbar_wait(&accf[c & 1], (c >> 1) & 1, s_err, args.err, 4));
       if (!ok) break;
       tc_fence_after();
-      const bool last = (c == nchunks - 1);
-      const bool drain1 = last || (c % kP1) == kP1 - 1;
-      const bool drain2 = last || (c % kP2) == kP2 - 1;
+      const int p = c / kP1;
+      const bool drain1 = (c % kP1) == kP1 - 1 || c == nchunks - 1;
       const uint32_t t0 = tmem_base + lane_off + (uint32_t)((c & 1) * BN + col0);
-      const uint32_t t1 = tmem_base + lane_off + (uint32_t)(2 * BN + col0);
-      const uint32_t t2 = tmem_base + lane_off + (uint32_t)(3 * BN + col0);
+      const uint32_t t1 = tmem_base + lane_off + (uint32_t)((2 + (p & 1)) * BN + col0);
 #pragma unroll
       for (int cb = 0; cb < kDrainCols / 4; ++cb) {
-        uint32_t v0[4], v1[4], v2[4];
+        uint32_t v0[4], v1[4];
         tmem_ld4(t0 + cb * 4, v0);
         if (drain1) tmem_ld4(t1 + cb * 4, v1);
-        if (drain2) tmem_ld4(t2 + cb * 4, v2);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int jj = cb * 4 + j;
           const float a0 = __uint_as_float(v0[j]);
-          // (H, L) += a0 with TwoSum on the high part
+          // (H, L) += a0 with TwoSum on the high part; g1 into the low part
           const float S = H[jj] + a0;
           const float bp = S - H[jj];
           const float e = (H[jj] - (S - bp)) + (a0 - bp);
           H[jj] = S;
           float l = L[jj] + e;
-          if (drain1) l = fmaf(__uint_as_float(v1[j]), 1.0f / 128.0f, l);
-          if (drain2) l = fmaf(__uint_as_float(v2[j]), 1.0f / 16384.0f, l);
+          if (drain1) l += __uint_as_float(v1[j]);
           L[jj] = l;
         }
       }
@@ -252,8 +234,7 @@ __global__ void __launch_bounds__(kSyrkThreads, 1)
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(&acce[c & 1]);
-        if (drain1) mbar_arrive(acce1);
-        if (drain2) mbar_arrive(acce2);
+        if (drain1) mbar_arrive(&acce1[p & 1]);
       }
     }
     if (ok) {
@@ -314,39 +295,39 @@ __global__ void rrow_scale_kernel(BView B, int64_t K, int* __restrict__ row_exp)
   if (threadIdx.x == 0) row_exp[a] = slice_exp(m);
 }
 
-// Three integer slices of v 2^ex (|v 2^ex| < 128): v 2^ex = s1 + s2/128 + s3/128^2 + r.
-__device__ __forceinline__ void slice3(float v, int ex, float& s1, float& s2, float& s3) {
+// Two slices of x = v 2^ex (|x| < 128): the integer s1 = rint(x) and the fp16
+// remainder s2 = fp16(x - s1); dd = x - s1 - s2 exactly (FP32).
+__device__ __forceinline__ void slice2(float v, int ex, float& s1, __half& s2, float& dd) {
   const float x = ldexpf(v, ex);
   s1 = rintf(x);
-  const float r1 = (x - s1) * 128.f;
-  s2 = rintf(r1);
-  s3 = rintf((r1 - s2) * 128.f);
+  const float r = x - s1;
+  s2 = __float2half_rn(r);
+  dd = r - __half2float(s2);
 }
 
 // Slices of the R rows for the sum positions j0 .. j0 + nq - 1, one block per
 // row a: columns 2 (jl nJ + J) and + 1 hold the (re, im) of B at (position
 // j0 + jl, J); columns beyond 2 nq nJ (up to the padded width K2) are zero.
-// With corr, the block also adds to corr[a] the products of the row with itself
-// that the six-product contraction leaves out, 2 s2 s3 / 128^3 + s3^2 / 128^4 per
-// value (in slice units): on E'_aa they are all of one sign, so dropping them
-// biases the diagonal (the off-diagonal ones average out); the finish adds corr.
+// With corr, the block also adds to corr[a] the part of E'_aa (in slice units)
+// that the slices do not represent, sum of x^2 - (s1 + s2)^2 = dd (2 x - dd), so
+// that the finish makes the diagonal exact; off the diagonal the representation
+// error is of either sign and averages out.
 __global__ void __launch_bounds__(256) rsplit_kernel(BView B, int64_t j0, int nq, int64_t K2,
                                                      const int* __restrict__ row_exp, __half* __restrict__ S1,
-                                                     __half* __restrict__ S2, __half* __restrict__ S3,
-                                                     double* __restrict__ corr) {
+                                                     __half* __restrict__ S2, double* __restrict__ corr) {
   const int64_t a = blockIdx.x, half = K2 / 2, ncol = (int64_t)nq * B.nJ;
   const int ex = row_exp[a];
   float d = 0.f;
   for (int64_t c2 = threadIdx.x; c2 < half; c2 += blockDim.x) {
     const float2 x = (c2 < ncol) ? B.at(a, j0 * B.nJ + c2) : make_float2(0.f, 0.f);
-    float r1, r2, r3, i1, i2, i3;
-    slice3(x.x, ex, r1, r2, r3);
-    slice3(x.y, ex, i1, i2, i3);
+    float r1, i1, rd, id;
+    __half r2, i2;
+    slice2(x.x, ex, r1, r2, rd);
+    slice2(x.y, ex, i1, i2, id);
     const int64_t at = a * K2 + 2 * c2;
     *reinterpret_cast<__half2*>(S1 + at) = __floats2half2_rn(r1, i1);
-    *reinterpret_cast<__half2*>(S2 + at) = __floats2half2_rn(r2, i2);
-    *reinterpret_cast<__half2*>(S3 + at) = __floats2half2_rn(r3, i3);
-    d += (2.f * (r2 * r3 + i2 * i3) + (r3 * r3 + i3 * i3) * (1.f / 128.f)) * (1.f / 2097152.f);
+    *reinterpret_cast<__half2*>(S2 + at) = __halves2half2(r2, i2);
+    d += rd * (2.f * ldexpf(x.x, ex) - rd) + id * (2.f * ldexpf(x.y, ex) - id);
   }
   if (!corr) return;
   __shared__ double sd[8];
@@ -887,11 +868,11 @@ cudaError_t syrk_tc_rowscale(cudaStream_t st, const float2* B, int64_t sQ, int64
 
 namespace {
 template <int BKt, int NST>
-cudaError_t syrk_launch(cudaStream_t st, __half* const sl[3], int64_t n2, int64_t K2, const int2* tiles_d,
+cudaError_t syrk_launch(cudaStream_t st, __half* const sl[tc::NSLICE], int64_t n2, int64_t K2, const int2* tiles_d,
                         int ntiles, void* ws, int accumulate, int* err) {
   using namespace tc;
-  CUtensorMap m[3];
-  for (int i = 0; i < 3; ++i)
+  CUtensorMap m[NSLICE];
+  for (int i = 0; i < NSLICE; ++i)
     if (!make_map(&m[i], sl[i], K2, n2, K2, BM, BKt)) return cudaErrorInvalidValue;
   const size_t smem = (size_t)NST * NSLICE * (BM + BN) * BKt * 2 + 1024 + 256;
   cudaError_t e = cudaFuncSetAttribute(syrk_tc_kernel<BKt, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -900,7 +881,7 @@ cudaError_t syrk_launch(cudaStream_t st, __half* const sl[3], int64_t n2, int64_
   float* wh = reinterpret_cast<float*>(ws);
   float* wl = wh + (size_t)ntiles * BN * BM;
   TileArgs args{tiles_d, wh, wl, (int)(K2 / BKt), accumulate, err};
-  syrk_tc_kernel<BKt, NST><<<ntiles, kSyrkThreads, smem, st>>>(m[0], m[1], m[2], m[0], m[1], m[2], args);
+  syrk_tc_kernel<BKt, NST><<<ntiles, kSyrkThreads, smem, st>>>(m[0], m[1], args);
   count_launch();
   return cudaGetLastError();
 }
@@ -922,9 +903,8 @@ cudaError_t syrk_tc_split(cudaStream_t st, const float2* B, int64_t sQ, int64_t 
   const int64_t K2 = round_up(2 * (int64_t)nq * nJ, BK);
   __half* S1 = reinterpret_cast<__half*>(split);
   __half* S2 = S1 + (size_t)n2 * K2;
-  __half* S3 = S2 + (size_t)n2 * K2;
   BView bv{B, sQ, sA, nJ, qmap};
-  rsplit_kernel<<<(unsigned)n2, 256, 0, st>>>(bv, j0, nq, K2, row_exp, S1, S2, S3, corr);
+  rsplit_kernel<<<(unsigned)n2, 256, 0, st>>>(bv, j0, nq, K2, row_exp, S1, S2, corr);
   count_launch();
   return cudaGetLastError();
 }
@@ -935,9 +915,9 @@ cudaError_t syrk_tc_mma(cudaStream_t st, void* split, int64_t n2, int nq, int64_
   if (n2 <= 0 || nq <= 0 || ntiles <= 0) return cudaSuccess;
   const int64_t K2 = round_up(2 * (int64_t)nq * nJ, BK);
   __half* S1 = reinterpret_cast<__half*>(split);
-  __half* const sl[3] = {S1, S1 + (size_t)n2 * K2, S1 + 2 * (size_t)n2 * K2};
-  return cfg == 1 ? syrk_launch<32, 4>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err)
-                  : syrk_launch<64, 2>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err);
+  __half* const sl[tc::NSLICE] = {S1, S1 + (size_t)n2 * K2};
+  return cfg == 1 ? syrk_launch<32, 6>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err)
+                  : syrk_launch<64, 3>(st, sl, n2, K2, tiles_d, ntiles, ws, accumulate, err);
 }
 
 constexpr int kEriBlocks = 152 * 16;  // fixed grid of the fused finish (reproducible traces)

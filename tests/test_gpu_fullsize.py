@@ -46,15 +46,17 @@ def c4_runs(cuda, lib_built):
         X = torch.empty((s["nk"], s["np"], s["nao"]), dtype=torch.complex128, device="cuda")
         g.get(0, X)
         g.fit_zeta(TAU)
-        g.coulomb_metric()
+        V = torch.empty((s["nk"], s["np"], s["np"]), dtype=torch.complex128, device="cuda")
+        g.coulomb_metric(V)
         dt = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
         Cs = [torch.from_numpy(f.C).cuda() for f in frags]
         gs = [torch.from_numpy(f.gamma).cuda() for f in frags]
         eris = [torch.empty((f.norb,) * 4, dtype=dt, device="cuda") for f in frags]
         ej, ek = g.fragment_eri(Cs, gs, eris)
         torch.cuda.synchronize()
-        out[prec] = dict(X=X.cpu().numpy(), eri=[e.cpu().numpy().astype(np.complex128) for e in eris],
-                         ej=ej, ek=ek)
+        out[prec] = dict(X=X.cpu().numpy(), V=V.cpu().numpy(),
+                         eri=[e.cpu().numpy().astype(np.complex128) for e in eris], ej=ej, ek=ek)
+        del V
         g.close()
     return wl, frags, ips, out
 
@@ -70,6 +72,25 @@ def test_interp_vectors_against_oracle(c4_runs):
     Xo = phi.transpose(0, 2, 1)
     Xg = out[B.ISDF_MIXED]["X"][ks]
     assert np.abs(Xg - Xo).max() <= 1e-13 * np.abs(Xo).max()
+
+
+def test_smallest_fragment_against_oracle(c4_runs):
+    """The whole smallest c4 fragment (ERIs, E_J, E_K) against the oracle's direct
+    k-sums (Eqs. 19-20) given the FP64 path's X^k and V^q, in both precisions, and
+    its E_J against the oracle's cheap-J identity (a^Q = sum gamma_pq M^Q_(pq),
+    E_J = sum_Q a^Q V^Q a^Q^H / 2Nk), which needs no ERIs."""
+    from paper_2601_16379_gb300 import binding as B
+    wl, frags, ips, out = c4_runs
+    d = out[B.ISDF_FP64]
+    f = frags[0]
+    ref = O.fragment_eri(d["X"], d["V"], f.C, wl.cell.kmesh)
+    rj, rk = O.traces(ref, f.gamma)
+    for prec, tol in ((B.ISDF_FP64, 1e-8), (B.ISDF_MIXED, MIXED_TOL)):
+        assert np.abs(out[prec]["eri"][0] - ref).max() < tol
+        assert abs(out[prec]["ej"][0] - rj) < tol and abs(out[prec]["ek"][0] - rk) < tol
+    M = O.pair_tensor(O.fragment_T(d["X"], f.C), wl.cell.kmesh)
+    cj = O.cheap_J(M, d["V"], f.gamma, wl.cell.nkpts)
+    assert abs(d["ej"][0] - cj) < 1e-8 and abs(out[B.ISDF_MIXED]["ej"][0] - cj) < MIXED_TOL
 
 
 def test_mixed_matches_fp64_path(c4_runs):

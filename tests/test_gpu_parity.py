@@ -247,11 +247,15 @@ def test_mixed_q_chunks_c2(cuda, lib_built, c2, qc):
         res[limit] = gpu_eri(cuda, g, [f], 1)
         g.close()
     one, chunked = res[None], res[qc * per_q]
-    # the ERIs are returned in complex64: allow two fp32 ulps at the largest entry;
-    # the traces are reduced in FP64 from E itself
+    # the ERIs are returned in complex64: allow two fp32 ulps at the largest entry.
+    # The traces are reduced in FP64 from E'; the exact g0 products are independent of
+    # the chunking, but the low-order group g1 (products with the fp16 remainders,
+    # 2^-7 of the total) accumulates in FP32, whose rounding depends on where the
+    # chunks start: ~2^-24 per accumulation, 1e-8 of E_J bounds it
     scale = np.abs(one[0][0]).max()
     assert np.abs(chunked[0][0] - one[0][0]).max() <= 2.4e-7 * scale
-    assert abs(chunked[1][0] - one[1][0]) < 1e-10 and abs(chunked[2][0] - one[2][0]) < 1e-10
+    tr = 1e-8 * abs(one[1][0])
+    assert abs(chunked[1][0] - one[1][0]) < tr and abs(chunked[2][0] - one[2][0]) < tr
     ref, (rj, rk) = o.eri(tol, f)
     assert np.abs(chunked[0][0] - ref).max() < MIXED_TOL
     assert abs(chunked[1][0] - rj) < MIXED_TOL and abs(chunked[2][0] - rk) < MIXED_TOL
@@ -565,8 +569,8 @@ def test_autotuned_tile_order_on_a_large_fragment(cuda, lib_built, c2):
 
 @pytest.mark.parametrize("pipeline,band", [(0, 12), (1, 12), (1, 5)])
 def test_tile_schedules_match_oracle(cuda, lib_built, c2, pipeline, band):
-    """Each pipeline of the tensor-core tile kernel (K rows of 64 fp16 in 2
-    stages, rows of 32 fp16 in 4 stages) and tile order gives the oracle's ERIs."""
+    """Each pipeline of the tensor-core tile kernel (K rows of 64 fp16 in 3
+    stages, rows of 32 fp16 in 6 stages) and tile order gives the oracle's ERIs."""
     from paper_2601_16379_gb300 import binding as B
     torch = cuda
     wl, o = c2

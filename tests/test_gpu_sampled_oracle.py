@@ -155,3 +155,47 @@ def test_c5_kmesh_fit_and_metric_sampled(cuda, lib_built):
     g.coulomb_metric(V)
     assert _rel(V.cpu().numpy()[qs], Vref) < 1e-8
     g.close()
+
+
+@pytest.mark.slow
+def test_c5_fullsize_fragment_eris_sampled(cuda, lib_built):
+    """c5 at its own size (Nk = 1000, 24^3 grid, N_P = 300) in the configuration
+    bench.py times (mixed path, tensor-core contraction, time-reversal pairing):
+    the ERIs of a 4-orbital block of the smallest and of the largest c5 fragment
+    against the oracle's direct k-sums (Eqs. 19-20), given the GPU's X^k and V^q
+    (the oracle cannot run a 24^3 fit at Nk = 1000 in test time; X is checked
+    against the oracle's lattice sums at sampled k).  A block's ERIs are those of
+    the sub-fragment of its orbitals, so every q and every k enters."""
+    from paper_2601_16379_gb300 import binding as B
+    torch = cuda
+    wl = W.workload("c5", with_fragments=False)
+    cell = wl.cell
+    nk, npp = cell.nkpts, wl.n_p
+    order = np.argsort(wl.frag_sizes)
+    frags = W.make_fragments(wl, [int(order[0]), int(order[-1])])
+    g = B.Isdf(cell, B.ISDF_MIXED)
+    ips = g.build_points(wl.n_p, wl.seed)
+    X = torch.empty((nk, npp, cell.nao), dtype=torch.complex128, device="cuda")
+    g.get(0, X)
+    g.fit_zeta(TAU)
+    V = torch.empty((nk, npp, npp), dtype=torch.complex128, device="cuda")
+    g.coulomb_metric(V)
+    Cs = [torch.from_numpy(f.C).cuda() for f in frags]
+    gs = [torch.from_numpy(f.gamma).cuda() for f in frags]
+    outs = [torch.empty((f.norb,) * 4, dtype=torch.complex64, device="cuda") for f in frags]
+    ej, ek = g.fragment_eri(Cs, gs, outs)
+    torch.cuda.synchronize()
+    Xh, Vh = X.cpu().numpy(), V.cpu().numpy()
+    del X, V
+    ks = [0, 333, 999]
+    phi = O.bloch_ao(cell, kidx=ks, pts=O.grid_points(cell)[ips])
+    assert _rel(Xh[ks], phi.transpose(0, 2, 1)) < 1e-13
+    for f, e, j, k in zip(frags, outs, ej, ek):
+        n = f.norb
+        sub = np.array([0, n // 3, (2 * n) // 3, n - 1])
+        idx = torch.as_tensor(sub, device="cuda")
+        blk = e[idx][:, idx][:, :, idx][:, :, :, idx].cpu().numpy().astype(np.complex128)
+        ref = O.fragment_eri(Xh, Vh, f.C[:, :, sub], cell.kmesh)
+        assert np.abs(blk - ref).max() < MIXED_TOL
+        assert j > 0 > k
+    g.close()
