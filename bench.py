@@ -199,6 +199,8 @@ def run_gpu(args, rank, world, local_rank):
     mine = P.fragment_partition([f.norb for f in wl.fragments], world)[rank]
     frags = [wl.fragments[i] for i in mine]
     g = B.Isdf(wl.cell, prec)
+    if args.tile_schedule:
+        g.set_tile_schedule(*[int(x) for x in args.tile_schedule.split(",")])
     dt_out = torch.complex64 if prec == B.ISDF_MIXED else torch.complex128
     Cs = [torch.from_numpy(f.C).cuda() for f in frags]
     gs = [torch.from_numpy(f.gamma).cuda() for f in frags]
@@ -512,6 +514,8 @@ def _overrides(args):
         o.append(f"grid {args.mesh}^3")
     if args.frag_sizes:
         o.append(f"fragments n_f = {args.frag_sizes}")
+    if getattr(args, "tile_schedule", None):
+        o.append(f"E' tile schedule {args.tile_schedule} (pipeline, band)")
     return f" (overridden: {', '.join(o)})" if o else ""
 
 
@@ -791,6 +795,8 @@ def main():
     ap.add_argument("--nk-scan", type=int, default=1, help="1: time the c5 fragment set on 2^3..8^3 k-meshes too")
     ap.add_argument("--kmesh", type=int, default=None, help="k-mesh side override (Nk scan)")
     ap.add_argument("--mesh", type=int, default=None, help="real-space grid side override (small profiling cases)")
+    ap.add_argument("--tile-schedule", type=str, default=None,
+                    help="pipeline,band of the E' tile kernel, fixed (no tuning), e.g. 0,12 for a profile")
     ap.add_argument("--frag-sizes", type=str, default=None,
                     help="comma-separated fragment sizes replacing the workload's (small profiling cases)")
     args = ap.parse_args()

@@ -64,8 +64,8 @@ typedef enum {
                    /* float grid FFT and V_xi on the tensor cores with four exact   */
                    /* fp16 slices; the fragment pair tensor and ERI contractions   */
                    /* (Eqs. 19-20) in reduced precision (FP32 transforms; fp16      */
-                   /* integer + remainder slices for E, ~2^-19 relative; four exact */
-                   /* 7-bit slices for B = M L, ~2^-28; both on the tensor cores)   */
+                   /* integer + remainder slices on the tensor cores, ~2^-19 for E  */
+                   /* and ~2^-30 for B = M L, relative)                             */
   ISDF_FP64_TC = 2 /* FP64-class results on the tensor cores: points and fit as in  */
                    /* ISDF_MIXED, V in FP64; the pair tensor in float-float (~2^-44), */
                    /* B = M L with five and E with four exact fp16 slices per       */
@@ -243,7 +243,7 @@ int isdf_set_workspace_limit(isdf_handle* h, uint64_t bytes);
 /* MIXED mode: schedule of the fragment contraction's tensor-core tiles.  The
  * lower-triangle tiles of E' are launched in bands of row blocks (the CTAs of
  * one wave then share their operand blocks in L2), by a kernel with one of two
- * pipelines (0: K rows of 64 fp16 in 2 stages; 1: rows of 32 fp16 in 4 stages).
+ * pipelines (0: K rows of 64 fp16 in 3 stages; 1: rows of 32 fp16 in 6 stages).
  * With autotuning on (default), the first call that meets a tile list of a new
  * size class times its first q-chunk with the schedules (pipeline, band) =
  * (0, 12), (1, 12), (1, 6), (1, 24) and keeps the fastest for that class on this

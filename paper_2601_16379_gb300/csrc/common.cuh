@@ -243,8 +243,9 @@ int vxi_tc_chunk(int rx, int ng, size_t budget);
 size_t vxi_tc_work_bytes(int rx, int ng, int qc);
 cudaError_t vxi_tc(cudaStream_t st, const ffcomplex* c, int64_t qs, int rx, int ng, int nq, double omega,
                    double2* V, int64_t ldv, int64_t vs, void* work, int qc, int* err);
-// B^q = M^q L^q (w_q^{1/2} folded into L) on the tensor cores with four exact
-// integer slices, over the structural nonzeros of L^q only: the rp = max_q r_q
+// B^q = M^q L^q (w_q^{1/2} folded into L) on the tensor cores with three slices
+// per operand (an integer and two fp16 remainders), over the structural nonzeros
+// of L^q only: the rp = max_q r_q
 // pivot columns perm_q[c] (c < rank_q) of M^q and the nj output columns.  M^q is
 // stored by position j in the sum (q = qmap[j]) with q stride sq; B^q is written
 // in place over it with row pitch nj.  prepare: slices of L for all q (once per

@@ -432,12 +432,13 @@ std::vector<std::vector<int>> fragment_groups(int n, const int32_t* n_orb, int n
 }
 
 // Schedule of the E' contraction: the pipeline of the tile kernel (cfg 0: K rows of
-// 64 fp16 in 2 stages; cfg 1: rows of 32 fp16 in 4 stages) and the band width of
+// 64 fp16 in 3 stages; cfg 1: rows of 32 fp16 in 6 stages) and the band width of
 // the tile order (row blocks per band, see syrk_tc_tiles).  Chosen per size class
-// of the tile list by timing the first q-chunk with each candidate on first use;
-// the choice is kept in the handle.  `trial(cfg, band)` runs that chunk (it
-// overwrites the workspace, so the caller's run of the chunk afterwards is
-// unaffected).
+// of the tile list by timing the first q-chunk with each candidate on first use,
+// after one untimed run of each pipeline (the first launch of a kernel pays its
+// module loading); the choice is kept in the handle.  `trial(cfg, band)` runs that
+// chunk (it overwrites the workspace, so the caller's run of the chunk afterwards
+// is unaffected).
 struct TileSchedule {
   int cfg, band;
 };
@@ -450,6 +451,8 @@ TileSchedule tuned_schedule(isdf_handle* h, int64_t ntiles, const std::function<
   for (const auto& e : h->tune_log)
     if (e.bucket == bucket) return {e.cfg, e.band};
   isdf_handle::TuneEntry t{bucket, ntiles, dflt.cfg, dflt.band, {0, 0, 0, 0}};
+  for (int cfg = 0; cfg < 2; ++cfg)
+    if (trial(cfg, kTileCandidates[0].band) != 0) return {-1, -1};
   float best = 1e30f;
   for (int i = 0; i < 4; ++i) {
     cudaEvent_t a = h->get_event(), b = h->get_event();
@@ -1010,7 +1013,7 @@ int isdf_fragment_eri(isdf_handle* h, int n_frag, const int32_t* n_orb, const vo
     const double2* Xz = (const double2*)h->buf("X");
     // element bytes of the pair rows Z (float / float-float) and of M^q, B^q
     const size_t zsz = tc64 ? sizeof(ffloat) : sizeof(float), msz = tc64 ? sizeof(ffcomplex) : sizeof(float2);
-    // B = M L on the tensor cores (four exact slices; five in FP64_TC) when the
+    // B = M L on the tensor cores (three remainder slices; five exact ones in FP64_TC) when the
     // 2 r_q gathered columns fit their exact accumulation, else on the
     // compensated SIMT GEMM
     const bool tc_ml = tc64 || mlgemm_tc_supported(rp);

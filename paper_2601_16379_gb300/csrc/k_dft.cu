@@ -363,34 +363,26 @@ __global__ void __launch_bounds__(256) kdft_real_cubic_kernel(const typename CT<
   const int ct = 1 << lct;
   const int64_t c0 = (int64_t)blockIdx.x << (lct + 1);  // 2 ct real columns per block
   if (vec) {
-    // 16-byte vectors: EPV working columns each; every vector lies wholly inside or
-    // outside [0, ncol) (ncol and c0 are multiples of 2 EPV)
+    // 16-byte vectors: EPV working columns each, copied global -> shared by cp.async so
+    // that the whole tile is in flight at once; every vector lies wholly inside or
+    // outside [0, ncol) (ncol and c0 are multiples of 2 EPV), and its shared slot
+    // (k << lct) + cv EPV + (k / L) padk is a multiple of EPV elements (padk is even
+    // when ct is), i.e. 16-byte aligned
     constexpr int EPV = 16 / (int)sizeof(T);
     const int vpr = ct / EPV, total = nk * vpr;
-    constexpr int kBatch = 8;
-    for (int b0 = threadIdx.x; b0 < total; b0 += 256 * kBatch) {
-      float4 buf[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int v = b0 + u * 256;
-        buf[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (v < total) {
-          const int k = v / vpr, cv = v % vpr;
-          const int64_t col = c0 + 2 * (int64_t)cv * EPV;
-          if (col < ncol) buf[u] = __ldg(reinterpret_cast<const float4*>(in + (int64_t)k * ncol + col));
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int v = b0 + u * 256;
-        if (v < total) {
-          const int k = v / vpr, cv = v % vpr;
-          const T* e = reinterpret_cast<const T*>(&buf[u]);
-#pragma unroll
-          for (int i = 0; i < EPV; ++i) s[cidx<T, L>(k, cv * EPV + i, lct, padk)] = e[i];
-        }
+    for (int v = threadIdx.x; v < total; v += blockDim.x) {
+      const int k = v / vpr, cv = v % vpr;
+      const int64_t col = c0 + 2 * (int64_t)cv * EPV;
+      T* dst = &s[cidx<T, L>(k, cv * EPV, lct, padk)];
+      if (col < ncol) {
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(in + (int64_t)k * ncol + col)
+                     : "memory");
+      } else {
+        *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
     for (int e = threadIdx.x; e < nk * 2 * ct; e += blockDim.x) {
       const int k = e >> (lct + 1), c2 = e & (2 * ct - 1);

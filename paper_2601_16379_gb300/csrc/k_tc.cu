@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(256) eri_traces_final_kernel(const double2* __
 }
 
 // ---------------------------------------------------------------------------
-// B^q = M^q L^q on the tensor cores with four exact slices.
+// B^q = M^q L^q on the tensor cores with three slices per operand.
 //
 // Only the structural nonzeros of L^q enter (see the top of the file): the
 // contraction runs over c < r_q with M^q's column perm_q[c] and L^q's row
@@ -528,21 +528,22 @@ __global__ void __launch_bounds__(256) eri_traces_final_kernel(const double2* __
 // small operand; the slices of M are written and streamed once).  M rows are
 // scaled by 2^e_a (largest gathered
 // component over the q of the sum in [64, 128)), L columns by 2^f_qJ per q; both
-// are cut into four integer slices v = s1 + s2/128 + s3/128^2 + s4/128^3
-// (28 bits: B = M W^T L_xi carries the cancellation of the ill-conditioned W,
-// and three slices, 21 bits, measurably degrade the traces).  Ten fp16
-// products feed four weight groups
-//   g0 = S1T1, g1 = S1T2 + S2T1, g2 = S1T3 + S2T2 + S3T1,
-//   g3 = S1T4 + S2T3 + S3T2 + S4T1;
-// with K' = 2 r <= kMlMaxK every partial sum of each group is an integer of
-// magnitude below 2^24 (g3: at most 3 * 2^13 per k), so the FP32 TMEM
-// accumulation is exact; the epilogue forms g0 + g1/2^7 + g2/2^14 + g3/2^21
-// once and rescales.
-constexpr int MSL = 4;                                     // slices per operand
+// are cut into an integer and two fp16 remainders,
+//     x = s1 + s2 + s3 + d,  s1 = rint(x),  s2 = fp16(x - s1),  s3 = fp16(x - s1 - s2),
+// about 30 significant bits (B = M W^T L_xi carries the cancellation of the
+// ill-conditioned W, so 19 bits measurably degrade the traces).  Six fp16
+// products feed three groups
+//   g0 = S1T1, g1 = S1T2 + S2T1, g2 = S1T3 + S2T2 + S3T1;
+// with K' = 2 r <= kMlMaxK every partial sum of g0 is an integer of magnitude
+// below 2^24, so its FP32 TMEM accumulation is exact; g1 and g2 are 2^-7 and
+// 2^-18 of it and accumulate in FP32 over at most kMlMaxK terms.  The epilogue
+// forms g0 + (g1 + g2) once and rescales.  Simulated on the c2 data against the
+// exact products: E_J within ~1e-9 Ha (four 7-bit slices with ten products: ~2e-8).
+constexpr int MSL = 3;                                     // slices per operand
 constexpr int MBN = 96;                                    // B' rows per tile (N of the MMA)
 constexpr int MBJ = MBN / 2;                               // complex columns of B per tile
 constexpr int MB_BYTES = MBN * BK * 2;                     // 12 KB per slice
-constexpr int MSTAGE_BYTES = MSL * (A_BYTES + MB_BYTES);   // 112 KB
+constexpr int MSTAGE_BYTES = MSL * (A_BYTES + MB_BYTES);   // 84 KB
 constexpr int kMlMaxK = 640;                               // K' bound for exact accumulation
 constexpr uint32_t kIdescMl = (1u << 4) | ((uint32_t)(MBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
@@ -558,9 +559,8 @@ struct MlArgs {
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     mlgemm_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
-                     const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mA4,
-                     const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
-                     const __grid_constant__ CUtensorMap mB3, const __grid_constant__ CUtensorMap mB4, MlArgs args) {
+                     const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mB1,
+                     const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, MlArgs args) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * MSTAGE_BYTES);
@@ -601,8 +601,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      const CUtensorMap* ma[MSL] = {&mA1, &mA2, &mA3, &mA4};
-      const CUtensorMap* mb[MSL] = {&mB1, &mB2, &mB3, &mB4};
+      const CUtensorMap* ma[MSL] = {&mA1, &mA2, &mA3};
+      const CUtensorMap* mb[MSL] = {&mB1, &mB2, &mB3};
       const int arow = ql * args.n2 + ti * BM, brow = slot * 2 * args.nj_pad + tj * MBN;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t g0 = tmem_base, g1 = tmem_base + MBN, g2 = tmem_base + 2 * MBN, g3 = tmem_base + 3 * MBN;
+      const uint32_t g0 = tmem_base, g1 = tmem_base + MBN, g2 = tmem_base + 2 * MBN;
       bool ok = true;
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
@@ -645,10 +645,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           umma_f16(g2, dA[0] + off, dB[2] + off, kIdescMl, acc);
           umma_f16(g2, dA[1] + off, dB[1] + off, kIdescMl, 1u);
           umma_f16(g2, dA[2] + off, dB[0] + off, kIdescMl, 1u);
-          umma_f16(g3, dA[0] + off, dB[3] + off, kIdescMl, acc);
-          umma_f16(g3, dA[1] + off, dB[2] + off, kIdescMl, 1u);
-          umma_f16(g3, dA[2] + off, dB[1] + off, kIdescMl, 1u);
-          umma_f16(g3, dA[3] + off, dB[0] + off, kIdescMl, 1u);
         }
         umma_commit(&empty[s]);
       }
@@ -670,19 +666,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int* fcol = args.col_exp + (int64_t)slot * args.nj_pad + tj * MBJ;
 #pragma unroll 1
     for (int cb = 0; cb < MBN / 32; ++cb) {
-      uint32_t v0[32] = {}, v1[32] = {}, v2[32] = {}, v3[32] = {};
+      uint32_t v0[32] = {}, v1[32] = {}, v2[32] = {};
       if (okw) {
         const uint32_t lo = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
         tmem_ld32(lo, v0);
         tmem_ld32(lo + MBN, v1);
         tmem_ld32(lo + 2 * MBN, v2);
-        tmem_ld32(lo + 3 * MBN, v3);
       }
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const float v = __uint_as_float(v0[j]) +
-                        (__uint_as_float(v1[j]) * (1.0f / 128.0f) +
-                         (__uint_as_float(v2[j]) * (1.0f / 16384.0f) + __uint_as_float(v3[j]) * (1.0f / 2097152.0f)));
+        const float v = __uint_as_float(v0[j]) + (__uint_as_float(v1[j]) + __uint_as_float(v2[j]));
         const int n = cb * 32 + j;
         tileS[r * kPitch + n] = ldexpf(v, -(ea + fcol[n >> 1]));
       }
@@ -712,19 +705,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 __device__ __forceinline__ float round_int(float x) { return rintf(x); }
 __device__ __forceinline__ double round_int(double x) { return rint(x); }
 
-// Four integer slices of v (|v| < 128): v = s1 + s2/128 + s3/128^2 + s4/128^3 + r.
+// Three slices of v (|v| < 128): the integer s1 = rint(v) and the fp16 remainders
+// s2 = fp16(v - s1), s3 = fp16(v - s1 - s2).
 template <typename R>
-__device__ __forceinline__ void slice4(R v, __half& h1, __half& h2, __half& h3, __half& h4) {
+__device__ __forceinline__ void slice3r(R v, __half& h1, __half& h2, __half& h3) {
   const R s1 = round_int(v);
-  const R r1 = (v - s1) * (R)128;
-  const R s2 = round_int(r1);
-  const R r2 = (r1 - s2) * (R)128;
-  const R s3 = round_int(r2);
-  const R r3 = (r2 - s3) * (R)128;
+  const R r1 = v - s1;
+  h2 = __float2half_rn((float)r1);
+  const R r2 = r1 - (R)__half2float(h2);
   h1 = __float2half_rn((float)s1);
-  h2 = __float2half_rn((float)s2);
-  h3 = __float2half_rn((float)s3);
-  h4 = __float2half_rn((float)round_int(r3));
+  h3 = __float2half_rn((float)r2);
 }
 
 // Row exponents of M over the gathered columns of the q-points of the sum:
@@ -751,7 +741,7 @@ __global__ void mrow_scale_kernel(const float2* __restrict__ M, int64_t sq, int 
 __global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, const int* __restrict__ qmap,
                               const int* __restrict__ perm, const int* __restrict__ rank, int64_t n2, int j0, int nq,
                               int Kp, const int* __restrict__ row_exp, __half* __restrict__ S1,
-                              __half* __restrict__ S2, __half* __restrict__ S3, __half* __restrict__ S4) {
+                              __half* __restrict__ S2, __half* __restrict__ S3) {
   const int64_t half = Kp / 2, total = (int64_t)nq * n2 * half;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t ql = e / (n2 * half), rem = e % (n2 * half);
@@ -760,14 +750,13 @@ __global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, 
     float2 v = make_float2(0.f, 0.f);
     if (c < rank[q]) v = M[(int64_t)(j0 + ql) * sq + a * np + perm[(int64_t)q * np + c]];
     const int ex = row_exp[a];
-    __half r1, r2, r3, r4, i1, i2, i3, i4;
-    slice4<float>(ldexpf(v.x, ex), r1, r2, r3, r4);
-    slice4<float>(ldexpf(v.y, ex), i1, i2, i3, i4);
+    __half r1, r2, r3, i1, i2, i3;
+    slice3r<float>(ldexpf(v.x, ex), r1, r2, r3);
+    slice3r<float>(ldexpf(v.y, ex), i1, i2, i3);
     const int64_t at = (ql * n2 + a) * Kp + 2 * c;
     *reinterpret_cast<__half2*>(S1 + at) = __halves2half2(r1, i1);
     *reinterpret_cast<__half2*>(S2 + at) = __halves2half2(r2, i2);
     *reinterpret_cast<__half2*>(S3 + at) = __halves2half2(r3, i3);
-    *reinterpret_cast<__half2*>(S4 + at) = __halves2half2(r4, i4);
   }
 }
 
@@ -779,7 +768,7 @@ __global__ void msplit_kernel(const float2* __restrict__ M, int64_t sq, int np, 
 __global__ void lslice_kernel(const double2* __restrict__ L, const double* __restrict__ sw, int np,
                               const int* __restrict__ perm, const int* __restrict__ rank, int nj, int nj_pad, int Kp,
                               __half* __restrict__ S1, __half* __restrict__ S2, __half* __restrict__ S3,
-                              __half* __restrict__ S4, int* __restrict__ col_exp) {
+                              int* __restrict__ col_exp) {
   const int q = blockIdx.y, J = blockIdx.x >> 1, part = blockIdx.x & 1;
   const double w = sw[q];
   const int r = rank[q];
@@ -804,13 +793,12 @@ __global__ void lslice_kernel(const double2* __restrict__ L, const double* __res
       re = part ? li : lr;
       im = part ? lr : -li;
     }
-    __half a1, a2, a3, a4, b1, b2, b3, b4;
-    slice4<double>(re, a1, a2, a3, a4);
-    slice4<double>(im, b1, b2, b3, b4);
+    __half a1, a2, a3, b1, b2, b3;
+    slice3r<double>(re, a1, a2, a3);
+    slice3r<double>(im, b1, b2, b3);
     *reinterpret_cast<__half2*>(S1 + row + 2 * c) = __halves2half2(a1, b1);
     *reinterpret_cast<__half2*>(S2 + row + 2 * c) = __halves2half2(a2, b2);
     *reinterpret_cast<__half2*>(S3 + row + 2 * c) = __halves2half2(a3, b3);
-    *reinterpret_cast<__half2*>(S4 + row + 2 * c) = __halves2half2(a4, b4);
   }
 }
 
@@ -952,7 +940,7 @@ cudaError_t syrk_tc_finish_eri_z(cudaStream_t st, const void* ws, int ntiles, co
   return finish_eri_impl<double2>(st, ws, ntiles, tile_of_d, orb, nf, row_exp, corr, scale, eri, gamma, part, out4);
 }
 
-// ---- B = M L on the tensor cores, four slices (host side)
+// ---- B = M L on the tensor cores, three slices (host side)
 int mlgemm_tc_kp(int rp) { return (int)tc::round_up(2 * (int64_t)rp, tc::BK); }
 int mlgemm_tc_nj_pad(int nj) { return (int)tc::round_up(nj, tc::MBJ); }
 bool mlgemm_tc_supported(int rp) { return rp > 0 && mlgemm_tc_kp(rp) <= tc::kMlMaxK; }
@@ -970,7 +958,7 @@ cudaError_t mlgemm_tc_prepare(cudaStream_t st, const double2* L, const double* s
   const size_t per = (size_t)nk * 2 * njp * Kp;
   __half* S1 = reinterpret_cast<__half*>(lsl);
   lslice_kernel<<<dim3(2 * njp, nk), 128, 0, st>>>(L, sw, np, perm, rank, nj, njp, Kp, S1, S1 + per, S1 + 2 * per,
-                                                    S1 + 3 * per, col_exp);
+                                                    col_exp);
   count_launch();
   return cudaGetLastError();
 }
@@ -992,7 +980,7 @@ cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* q
   const size_t pa = (size_t)nq * n2 * Kp, pb = (size_t)nk * 2 * njp * Kp;
   __half* S1 = reinterpret_cast<__half*>(split);
   msplit_kernel<<<nblk((int64_t)nq * n2 * (Kp / 2)), 256, 0, st>>>(M, sq, np, qmap, perm, rank, n2, j0, nq, Kp,
-                                                                   row_exp, S1, S1 + pa, S1 + 2 * pa, S1 + 3 * pa);
+                                                                   row_exp, S1, S1 + pa, S1 + 2 * pa);
   count_launch();
   const __half* L1 = reinterpret_cast<const __half*>(lsl);
   CUtensorMap mA[MSL], mB[MSL];
@@ -1005,8 +993,7 @@ cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* q
   if (e != cudaSuccess) return e;
   const int mt = (int)((n2 + BM - 1) / BM), ntj = njp / MBJ;
   MlArgs args{M, qmap, row_exp, col_exp, sq, (int)n2, nj, njp, j0, Kp / BK, err};
-  mlgemm_tc_kernel<<<dim3(mt * ntj, nq), NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mA[3], mB[0], mB[1], mB[2],
-                                                                mB[3], args);
+  mlgemm_tc_kernel<<<dim3(mt * ntj, nq), NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], args);
   count_launch();
   return cudaGetLastError();
 }

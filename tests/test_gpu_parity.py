@@ -235,7 +235,7 @@ def test_mixed_q_chunks_c2(cuda, lib_built, c2, qc):
     f = wl.fragments[0]
     n2, np_ = f.norb ** 2, wl.n_p
     k2 = -(-2 * np_ // 64) * 64                 # fp16 columns of one q-point, padded to 64
-    per_q = 4 * (2 * n2) * k2 * 2 + 256           # four slices (B = M L) of the 2 n2 real rows
+    per_q = 3 * n2 * k2 * 2 + 256                 # three slices of M (B = M L), the larger per-q buffer
     res = {}
     for limit in (None, qc * per_q):
         g = B.Isdf(wl.cell, B.ISDF_MIXED)
