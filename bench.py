@@ -112,15 +112,15 @@ class ClockSampler:
 # Source regions of the dominant kernels: a committed ncu summary applies only
 # while the kernel's own source is the one it was taken on.
 KERNEL_REGIONS = {
-    "syrk_tc_kernel<64, 3>": ("k_tc.cu", "template <int BKt, int NST>\n__global__ void __launch_bounds__(kSyrkThreads, 1)\n"
-                              "    syrk_tc_kernel(", "// ----------------------------------------------------------------- helpers"),
+    "syrk_tc_kernel": ("k_tc.cu", "template <int BKt, int NST>\n__global__ void __launch_bounds__(kSyrkThreads, 1)\n"
+                       "    syrk_tc_kernel(", "// ----------------------------------------------------------------- helpers"),
     "syrk4_tc_kernel": ("k_tc64.cu", "__global__ void __launch_bounds__(NT4, 1)\n    syrk4_tc_kernel(",
                         "// B viewed as element"),
 }
 
 
 def kernel_source_hash(kernel: str):
-    f, start, end = KERNEL_REGIONS[kernel]
+    f, start, end = KERNEL_REGIONS[kernel.split("<")[0]]
     src = (ROOT / "paper_2601_16379_gb300" / "csrc" / f).read_text()
     i = src.find(start)
     j = src.find(end, i + 1)
@@ -147,6 +147,13 @@ def profile_traffic(kernel: str, flops_per_launch: float):
         if k and m and t and k.group(1).strip() == kernel and m.group(1) == h:
             return float(t.group(1)) * flops_per_launch, prof.name
     return None, None
+
+
+def syrk_variant(report):
+    """Template instance of the mixed E' kernel that the tile-schedule tuner chose for
+    the largest tile list (the largest fragments carry most of the flops)."""
+    pipeline = max(report, key=lambda e: e["tiles"])["pipeline"] if report else 0
+    return "syrk_tc_kernel<32, 6>" if pipeline == 1 else "syrk_tc_kernel<64, 3>"
 
 
 def reduce_max_over_ranks(values, dist, device):
@@ -326,7 +333,8 @@ def run_gpu(args, rank, world, local_rank):
     herk_avg_ms = herk_ms / max(herk_n, 1)
     traffic, traffic_src = None, None
     if herk_n and kernel_name.startswith("syrk"):
-        kname = "syrk4_tc_kernel" if prec == B.ISDF_FP64_TC else "syrk_tc_kernel<64, 3>"
+        fixed = [{"tiles": 0, "pipeline": int(args.tile_schedule.split(",")[0])}] if args.tile_schedule else None
+        kname = "syrk4_tc_kernel" if prec == B.ISDF_FP64_TC else syrk_variant(fixed or g.autotune_report())
         traffic, prof = profile_traffic(kname, herk_flops / herk_n)
         if traffic is not None:
             traffic_src = (f"{prof}: DRAM bytes per algorithmic flop of a small-case capture of {kname}, "

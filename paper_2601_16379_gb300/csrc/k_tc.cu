@@ -68,7 +68,6 @@ constexpr int BN = 128;        // B' rows per tile (complex columns of E)
 constexpr int BK = 64;         // fp16 per row per stage (one 128-byte swizzle row)
 constexpr int STAGES = 2;                   // B = M L pipeline depth
 constexpr int NSLICE = 2;                   // fp16 slices per value in E': s1 (integer), s2 (remainder)
-constexpr int A_BYTES = BM * BK * 2;        // 16 KB per slice
 constexpr int TMEM_COLS = 512;              // g0 and g1, each two 128-column FP32 buffers
 constexpr int NTHREADS = 192;
 // E' kernel: warp 0 TMA, warp 1 MMA, 16 drain warps (TMEM lane quarter warp % 4, 32 of
@@ -539,11 +538,17 @@ __global__ void __launch_bounds__(256) eri_traces_final_kernel(const double2* __
 // 2^-18 of it and accumulate in FP32 over at most kMlMaxK terms.  The epilogue
 // forms g0 + (g1 + g2) once and rescales.  Simulated on the c2 data against the
 // exact products: E_J within ~1e-9 Ha (four 7-bit slices with ten products: ~2e-8).
+// Tiles of 128 x 64 with K rows of 32 fp16 in two stages: 72 KB of shared memory and
+// 256 TMEM columns per CTA, so that two CTAs share an SM and one's set-up and
+// epilogue overlap the other's MMAs (each tile runs only 2 r_q / 32 k-blocks).
 constexpr int MSL = 3;                                     // slices per operand
-constexpr int MBN = 96;                                    // B' rows per tile (N of the MMA)
+constexpr int MBN = 64;                                    // B' rows per tile (N of the MMA)
 constexpr int MBJ = MBN / 2;                               // complex columns of B per tile
-constexpr int MB_BYTES = MBN * BK * 2;                     // 12 KB per slice
-constexpr int MSTAGE_BYTES = MSL * (A_BYTES + MB_BYTES);   // 84 KB
+constexpr int MBK = 32;                                    // fp16 of K per stage row (64-byte swizzle)
+constexpr int MA_BYTES = BM * MBK * 2;                     // 8 KB per slice
+constexpr int MB_BYTES = MBN * MBK * 2;                    // 4 KB per slice
+constexpr int MSTAGE_BYTES = MSL * (MA_BYTES + MB_BYTES);  // 36 KB
+constexpr int kMlTmem = 256;                               // three 64-column groups
 constexpr int kMlMaxK = 640;                               // K' bound for exact accumulation
 constexpr uint32_t kIdescMl = (1u << 4) | ((uint32_t)(MBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
@@ -557,7 +562,7 @@ struct MlArgs {
   int* err;
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, 2)
     mlgemm_tc_kernel(const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mA2,
                      const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mB1,
                      const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, MlArgs args) {
@@ -590,7 +595,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
-                 "r"(TMEM_COLS)
+                 "r"(kMlTmem)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -609,11 +614,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&empty[s], (r & 1) ^ 1, s_err, args.err, 11)) break;
         uint8_t* st = smem + s * MSTAGE_BYTES;
         mbar_expect_tx(&full[s], MSTAGE_BYTES);
-        const int x = kb * BK;
+        const int x = kb * MBK;
 #pragma unroll
         for (int i = 0; i < MSL; ++i) {
-          tma_load_2d(st + i * A_BYTES, ma[i], &full[s], x, arow);
-          tma_load_2d(st + MSL * A_BYTES + i * MB_BYTES, mb[i], &full[s], x, brow);
+          tma_load_2d(st + i * MA_BYTES, ma[i], &full[s], x, arow);
+          tma_load_2d(st + MSL * MA_BYTES + i * MB_BYTES, mb[i], &full[s], x, brow);
         }
       }
     }
@@ -632,11 +637,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint64_t dA[MSL], dB[MSL];
 #pragma unroll
         for (int i = 0; i < MSL; ++i) {
-          dA[i] = sdesc_sw128(st + i * A_BYTES);
-          dB[i] = sdesc_sw128(st + MSL * A_BYTES + i * MB_BYTES);
+          dA[i] = sdesc_k<MBK>(st + i * MA_BYTES);
+          dB[i] = sdesc_k<MBK>(st + MSL * MA_BYTES + i * MB_BYTES);
         }
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
+        for (int kk = 0; kk < MBK / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;
           const uint32_t acc = (kb == 0 && kk == 0) ? 0u : 1u;
           umma_f16(g0, dA[0] + off, dB[0] + off, kIdescMl, acc);
@@ -697,7 +702,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kMlTmem)
                  : "memory");
   }
 }
@@ -985,14 +990,14 @@ cudaError_t mlgemm_tc_chunk(cudaStream_t st, float2* M, int64_t sq, const int* q
   const __half* L1 = reinterpret_cast<const __half*>(lsl);
   CUtensorMap mA[MSL], mB[MSL];
   for (int i = 0; i < MSL; ++i)
-    if (!make_map(&mA[i], S1 + i * pa, Kp, (int64_t)nq * n2, Kp, BM) ||
-        !make_map(&mB[i], L1 + i * pb, Kp, (int64_t)nk * 2 * njp, Kp, MBN))
+    if (!make_map(&mA[i], S1 + i * pa, Kp, (int64_t)nq * n2, Kp, BM, MBK) ||
+        !make_map(&mB[i], L1 + i * pb, Kp, (int64_t)nk * 2 * njp, Kp, MBN, MBK))
       return cudaErrorInvalidValue;
   const size_t smem = (size_t)STAGES * MSTAGE_BYTES + 1024 + 256;
   cudaError_t e = cudaFuncSetAttribute(mlgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int mt = (int)((n2 + BM - 1) / BM), ntj = njp / MBJ;
-  MlArgs args{M, qmap, row_exp, col_exp, sq, (int)n2, nj, njp, j0, Kp / BK, err};
+  MlArgs args{M, qmap, row_exp, col_exp, sq, (int)n2, nj, njp, j0, Kp / MBK, err};
   mlgemm_tc_kernel<<<dim3(mt * ntj, nq), NTHREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], args);
   count_launch();
   return cudaGetLastError();
