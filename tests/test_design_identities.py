@@ -10,6 +10,10 @@ check on the oracle's pair tensor and Coulomb metric:
 * the real symmetric form: in the basis u = e_(pq) + e_(qp), v = i (e_(pq) - e_(qp)),
   e_(pp) fixed by the time-reversal symmetry E_{s(a)s(b)} = conj(E_ab), E is real,
   and equals c sum_{q in S} [Re R^q, Im R^q][Re R^q, Im R^q]^T over the half set S.
+
+The last two tests model the fp16 slice arithmetic of the tensor-core
+contractions (E' and B = M L) and check the exactness and error bounds they
+rely on.
 """
 import numpy as np
 import pytest
@@ -122,3 +126,72 @@ def test_structural_zeros_of_the_coulomb_factor():
         # and it reproduces V^q
         assert np.abs(Lq @ Lq.conj().T - r["V"][q]).max() < 1e-8 * np.abs(r["V"][q]).max()
     assert seen_truncated
+
+
+# ------------------------------------------------------------ slice arithmetic
+# The tensor-core contractions of the mixed path write each scaled value x
+# (|x| < 128 after the per-row power-of-two scaling) as fp16 slices whose
+# products the tcgen05 MMA accumulates in FP32.  These tests model that
+# arithmetic in numpy (fp16 rounding of the slices, exact FP64 products) and
+# check the facts the kernels rely on.
+
+def _scaled_rows(rng, n, k):
+    """Rows of mixed magnitude, each scaled by a power of two so that its largest
+    entry lies in [64, 128), as the slicing kernels do; also returns the scales."""
+    R = rng.standard_normal((n, k)) * np.exp(rng.uniform(-6.0, 6.0, size=(n, 1)))
+    R[:, ::7] *= 1e-3                                    # small entries inside a row
+    e = 6 - np.floor(np.log2(np.abs(R).max(axis=1)))
+    return (R * 2.0 ** e[:, None]).astype(np.float32).astype(np.float64), 2.0 ** e
+
+
+def _f16(x):
+    return x.astype(np.float16).astype(np.float64)
+
+
+def test_e_prime_two_slice_form():
+    """E' = R R^T from s1 = rint(x) and s2 = fp16(x - s1): the g0 products are
+    integers whose partial sums over a 1024-step chunk stay within 2^24 (so their
+    FP32 accumulation is exact), the diagonal correction sum x^2 - (s1 + s2)^2
+    makes E'_aa exact, and off the diagonal the four products are within 2^-18 of
+    |R_a||R_b|."""
+    rng = np.random.default_rng(5)
+    X, _ = _scaled_rows(rng, 24, 2048)
+    assert np.abs(X).max() < 128.0 and np.all(np.abs(X).max(axis=1) >= 64.0)
+    s1 = np.rint(X)
+    s2 = _f16(X - s1)
+    assert np.abs(s1).max() <= 128 and np.abs(s2).max() <= 0.5
+    g0 = s1 @ s1.T
+    chunk = 1024
+    worst = max(np.abs(s1[:, c:c + chunk]).sum(axis=1).max() for c in range(0, X.shape[1], chunk))
+    assert worst * 128.0 <= 2.0 ** 24                    # any partial sum of a chunk is an exact FP32 integer
+    Ep = g0 + s1 @ s2.T + s2 @ s1.T + s2 @ s2.T
+    corr = (X ** 2).sum(axis=1) - ((s1 + s2) ** 2).sum(axis=1)
+    Ep[np.diag_indices_from(Ep)] += corr
+    E = X @ X.T
+    nrm = np.sqrt(np.outer((X ** 2).sum(1), (X ** 2).sum(1)))
+    assert np.allclose(np.diag(Ep), np.diag(E), rtol=1e-13, atol=0)   # FP64 summation order only
+    assert np.abs(Ep - E).max() / nrm.max() < 2.0 ** -18
+    # the remainder's fp16 rounding: unit roundoff 2^-11 of |s2| (2^-25 below fp16's
+    # normal range), i.e. ~19 significant bits per value with |x| in [64, 128)
+    assert np.all(np.abs(X - s1 - s2) <= 2.0 ** -11 * np.abs(s2) + 2.0 ** -25)
+
+
+def test_b_three_slice_form():
+    """B = M L from an integer and two fp16 remainders per operand (six products,
+    i + j <= 2): g0 = S1 T1 stays an exact FP32 integer sum for 2 r_q <= 640, and
+    the result is within 2^-26 of |M_a||L_J| (B carries the cancellation of the
+    ill-conditioned factor, so the bound is on the operands, not on B)."""
+    rng = np.random.default_rng(6)
+    A, sa = _scaled_rows(rng, 16, 640)
+    Bt, sb = _scaled_rows(rng, 12, 640)
+    def sl(x):
+        s1 = np.rint(x)
+        s2 = _f16(x - s1)
+        s3 = _f16(x - s1 - s2)
+        return [s1, s2, s3]
+    a, b = sl(A), sl(Bt)
+    assert 640 * 128.0 * 128.0 <= 2.0 ** 24
+    prod = sum(a[i] @ b[j].T for i in range(3) for j in range(3) if i + j <= 2)
+    ref = A @ Bt.T
+    nrm = np.sqrt(np.outer((A ** 2).sum(1), (Bt ** 2).sum(1)))
+    assert np.abs(prod - ref).max() / nrm.max() < 2.0 ** -26
