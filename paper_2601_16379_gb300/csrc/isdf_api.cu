@@ -801,7 +801,7 @@ int isdf_coulomb_metric(isdf_handle* h, void* V_out) {
   if (int e = check_device(h)) return e;
   if (!h->has_fit || !h->has_xi) return fail(h, ISDF_ERR_STATE, "isdf_coulomb_metric before isdf_fit_zeta");
   const int nk = h->nk, np = h->np, ng = h->ng;
-  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  const double2 zero = make_double2(0.0, 0.0);
   double2* xi = (double2*)h->buf("xi");
   double2* W = (double2*)h->buf("W");
   const double2* tw = (const double2*)h->buf("grid_tw");
