@@ -11,9 +11,11 @@ check on the oracle's pair tensor and Coulomb metric:
   e_(pp) fixed by the time-reversal symmetry E_{s(a)s(b)} = conj(E_ab), E is real,
   and equals c sum_{q in S} [Re R^q, Im R^q][Re R^q, Im R^q]^T over the half set S.
 
-The last two tests model the fp16 slice arithmetic of the tensor-core
-contractions (E' and B = M L) and check the exactness and error bounds they
-rely on.
+Two tests model the fp16 slice arithmetic of the tensor-core contractions (E'
+and B = M L) and check the exactness and error bounds they rely on; the last
+restates the fused finish's 2 x 2 block formulas (E' -> chemist-order ERIs and
+the J/K trace terms) and checks them against the direct map and the oracle's
+traces.
 """
 import numpy as np
 import pytest
@@ -195,3 +197,84 @@ def test_b_three_slice_form():
     ref = A @ Bt.T
     nrm = np.sqrt(np.outer((A ** 2).sum(1), (Bt ** 2).sum(1)))
     assert np.abs(prod - ref).max() / nrm.max() < 2.0 ** -26
+
+
+def _block_formulas(Ep, gamma, nf):
+    """The E' -> ERI map and the trace terms of the fused finish, block by block:
+    orbit o (pair p < q: rows u = 2 o, v = 2 o + 1; diagonal p: row 2 P + p), the
+    block of two orbits U = E'(u1, u2), X = E'(u1, v2), Y = E'(v1, u2), Z = E'(v1, v2),
+    and the real-part trace formulas for a Hermitian gamma."""
+    pairs = [(p, q) for p in range(nf) for q in range(p + 1, nf)]
+    P = len(pairs)
+    orbs = pairs + [(p, p) for p in range(nf)]
+    row = lambda o: 2 * o if o < P else 2 * P + (o - P)
+    eri = np.zeros((nf,) * 4, complex)
+    aj = ak = 0.0
+    g = gamma
+    for o1, (p, q) in enumerate(orbs):
+        for o2, (x, y) in enumerate(orbs):
+            u1, u2 = row(o1), row(o2)
+            pr, pc = p != q, x != y
+            U = Ep[u1, u2]
+            X = Ep[u1, u2 + 1] if pc else 0.0
+            Y = Ep[u1 + 1, u2] if pr else 0.0
+            Z = Ep[u1 + 1, u2 + 1] if pr and pc else 0.0
+            if pr and pc:
+                r1, i1, r2, i2 = (U + Z) / 4, (Y - X) / 4, (U - Z) / 4, (X + Y) / 4
+                eri[p, q, y, x], eri[p, q, x, y] = r1 + 1j * i1, r2 + 1j * i2
+                eri[q, p, y, x], eri[q, p, x, y] = r2 - 1j * i2, r1 - 1j * i1
+                A, B = g[p, q], g[y, x]
+                aj += U * A.real * B.real - Z * A.imag * B.imag + X * A.real * B.imag - Y * A.imag * B.real
+                w1, w2 = g[p, x] * g[y, q], g[p, y] * g[x, q]
+                ak += 2 * (w1.real * r1 - w1.imag * i1 + w2.real * r2 - w2.imag * i2)
+            elif pr:
+                r, im = U / 2, Y / 2
+                eri[p, q, x, x], eri[q, p, x, x] = r + 1j * im, r - 1j * im
+                A = g[p, q]
+                aj += g[x, x].real * (A.real * U - A.imag * Y)
+                w = g[p, x] * g[x, q]
+                ak += 2 * (w.real * r - w.imag * im)
+            elif pc:
+                r, im = U / 2, -X / 2
+                eri[p, p, y, x], eri[p, p, x, y] = r + 1j * im, r - 1j * im
+                B = g[y, x]
+                aj += g[p, p].real * (B.real * U + B.imag * X)
+                w = g[p, x] * g[y, p]
+                ak += 2 * (w.real * r - w.imag * im)
+            else:
+                eri[p, p, x, x] = U
+                w = g[p, x]
+                aj += g[p, p].real * g[x, x].real * U
+                ak += abs(w) ** 2 * U
+    return eri, 0.5 * aj, -0.25 * ak
+
+
+def test_finish_block_formulas_equal_direct_map():
+    """The finish never forms E: it maps each 2 x 2 block of the real E' straight to
+    chemist-order ERIs and trace terms.  On a random real symmetric E' and a random
+    Hermitian gamma those formulas equal E = T^-1 E' T^-H with the time-reversal
+    basis rows u = e_(pq) + e_(qp), v = -i (e_(pq) - e_(qp)), e_(pp), the chemist
+    order (pq|rs) = E_(pq),(sr), and the oracle's direct traces."""
+    rng = np.random.default_rng(8)
+    nf = 5
+    n2 = nf * nf
+    pairs = [(p, q) for p in range(nf) for q in range(p + 1, nf)]
+    T = np.zeros((n2, n2), complex)
+    for o, (p, q) in enumerate(pairs):
+        T[2 * o, p * nf + q] = T[2 * o, q * nf + p] = 1.0
+        T[2 * o + 1, p * nf + q], T[2 * o + 1, q * nf + p] = -1j, 1j
+    for p in range(nf):
+        T[2 * len(pairs) + p, p * nf + p] = 1.0
+    A = rng.standard_normal((n2, n2))
+    Ep = A @ A.T
+    Ti = np.linalg.inv(T)
+    E = Ti @ Ep @ Ti.conj().T
+    s = np.array([q * nf + p for p in range(nf) for q in range(nf)])   # (pq) -> (qp)
+    assert np.allclose(E[np.ix_(s, s)], E.conj())                       # the time-reversal symmetry
+    ref = O.eri_from_E(E, nf)
+    G = rng.standard_normal((nf, nf)) + 1j * rng.standard_normal((nf, nf))
+    gamma = G @ G.conj().T
+    rj, rk = O.traces(ref, gamma)
+    eri, ej, ek = _block_formulas(Ep, gamma, nf)
+    assert np.abs(eri - ref).max() < 1e-12 * np.abs(ref).max()
+    assert abs(ej - rj) < 1e-11 * abs(rj) and abs(ek - rk) < 1e-11 * abs(rk)
