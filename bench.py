@@ -149,6 +149,18 @@ def profile_traffic(kernel: str, flops_per_launch: float):
     return None, None
 
 
+def any_rank(flag: bool, dist, device) -> bool:
+    """True on every rank if it is true on any rank.  The budget decisions that end
+    the warm-up and timed loops are taken this way: each step ends in a collective
+    (the trace gather), so all ranks must run the same number of steps."""
+    if dist is None:
+        return bool(flag)
+    import torch
+    t = torch.tensor([1.0 if flag else 0.0], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return bool(t.item() > 0.5)
+
+
 def syrk_variant(report):
     """Template instance of the mixed E' kernel that the tile-schedule tuner chose for
     the largest tile list (the largest fragments carry most of the flops)."""
@@ -247,7 +259,8 @@ def run_gpu(args, rank, world, local_rank):
     warm = []
     want_w = args.warmup
     for i in range(want_w):
-        if i >= min(want_w, MIN_WARMUP) and warm and budget.left() < warm[-1] * (2 + 1.5) + args.reserve_s:
+        if i >= min(want_w, MIN_WARMUP) and any_rank(
+                bool(warm) and budget.left() < warm[-1] * (2 + 1.5) + args.reserve_s, dist, "cuda"):
             break
         t0 = time.perf_counter()
         step(Cs, gs, outs)
@@ -269,7 +282,7 @@ def run_gpu(args, rank, world, local_rank):
     evs[0].record(st)
     done = 0
     while done < args.steps:
-        if done >= 1 and budget.left() < t_step * (1 + 1.5) + args.reserve_s:
+        if done >= 1 and any_rank(budget.left() < t_step * (1 + 1.5) + args.reserve_s, dist, "cuda"):
             break
         ej, ek = step(Cs, gs, outs)
         e = torch.cuda.Event(enable_timing=True)

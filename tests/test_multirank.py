@@ -40,9 +40,29 @@ def test_timings_reduce_to_the_slowest_rank():
         assert out[r] == [2.0, 10.0]
 
 
+def _any_rank_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    # rank 1 alone runs out of budget: every rank stops; nobody out of budget: nobody stops
+    out[rank] = (bench.any_rank(rank == 1, dist, "cpu"), bench.any_rank(False, dist, "cpu"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_budget_decisions_agree_across_ranks():
+    """Each bench step ends in a collective, so the wall-clock budget that stops the
+    warm-up and timed loops is decided jointly: one rank out of budget stops all."""
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_any_rank_worker, args=(world, port, out), nprocs=world, join=True)
+    assert [out[r] for r in range(world)] == [(True, False)] * world
+
+
 def test_single_process_is_identity():
     import bench
     assert bench.reduce_max_over_ranks([3.5, 4.25], None, "cpu") == [3.5, 4.25]
+    assert bench.any_rank(True, None, "cpu") is True and bench.any_rank(False, None, "cpu") is False
 
 
 # ------------------------------------------------- fragment partition
